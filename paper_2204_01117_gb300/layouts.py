@@ -1,0 +1,260 @@
+"""Seeded synthetic urban layouts (porosity fields) for the RANS step.
+
+This module only generates inputs.  It holds none of the solver's arithmetic
+and imports nothing from the rest of the package, so the CUDA path and the
+test oracle can both be fed from it.
+
+Porosity follows the paper's unified model: phi = 1 in air, phi = 0 inside a
+solid building, phi in (0, 1) inside a porous tree canopy (Sec. 3 footnote;
+App. A.2), and cut cells get the fraction of a uniform 4x4x4 sub-sample that
+lies outside the objects (Sec. 3, "Urban model resolving").  Where objects
+overlap, a sub-sample takes the smallest porosity of the objects that hold it.
+
+Random draws come from SplitMix64 (Steele, Lea and Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014): the state advances by
+0x9E3779B97F4A7C15 and each output is the state passed through the two
+xor-shift-multiply rounds of that paper.  A uniform double in [0, 1) takes the
+top 53 bits of one output.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_MASK = (1 << 64) - 1
+
+
+class SplitMix64:
+    """SplitMix64 stream; ``next_u64`` returns successive 64-bit outputs."""
+
+    def __init__(self, seed: int):
+        self.state = seed & _MASK
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & _MASK
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+        return z ^ (z >> 31)
+
+    def uniform(self, lo: float = 0.0, hi: float = 1.0) -> float:
+        return lo + (hi - lo) * ((self.next_u64() >> 11) * (1.0 / (1 << 53)))
+
+    def randint(self, lo: int, hi: int) -> int:
+        """Integer uniform on [lo, hi] inclusive (multiply-shift on 32 high bits)."""
+        span = hi - lo + 1
+        return lo + (((self.next_u64() >> 32) * span) >> 32)
+
+
+@dataclass
+class Box:
+    x0: float
+    x1: float
+    y0: float
+    y1: float
+    z0: float
+    z1: float
+    phi: float = 0.0
+
+
+@dataclass
+class Ellipsoid:
+    cx: float
+    cy: float
+    cz: float
+    rx: float
+    ry: float
+    rz: float
+    phi: float = 0.5
+
+
+@dataclass
+class Scenario:
+    """Grid, inflow and porosity of one synthetic run."""
+    nx: int
+    ny: int
+    nz: int
+    h: float
+    phi: np.ndarray                     # (nz, ny, nx) float64
+    wind_dir_deg: float = 0.0
+    u_ref: float = 5.0
+    z_ref: float = 10.0
+    z0: float = 0.5
+    inflow_loglaw: bool = False
+    ground_noslip: bool = True
+    steps: int = 100
+    name: str = ""
+    objects: list = field(default_factory=list)
+
+    def params(self) -> dict:
+        """Physical parameters shared by every solver that runs this input."""
+        return dict(h=self.h, wind_dir_deg=self.wind_dir_deg, u_ref=self.u_ref,
+                    z_ref=self.z_ref, z0=self.z0, inflow_loglaw=int(self.inflow_loglaw),
+                    ground_noslip=int(self.ground_noslip))
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+def rasterize(nx: int, ny: int, nz: int, h: float, objects, sub: int = 4) -> np.ndarray:
+    """Cell porosity from objects by sub-sampling each cell sub^3 times."""
+    phi = np.ones((nz, ny, nx), dtype=np.float64)
+    off = (np.arange(sub) + 0.5) / sub
+    xs = ((np.arange(nx)[:, None] + off[None, :]) * h).reshape(-1)   # nx*sub
+    ys = ((np.arange(ny)[:, None] + off[None, :]) * h).reshape(-1)
+    for k in range(nz):
+        zs = (k + off) * h                                            # sub
+        touching = []
+        for ob in objects:
+            if isinstance(ob, Box):
+                lo, hi = ob.z0, ob.z1
+            else:
+                lo, hi = ob.cz - ob.rz, ob.cz + ob.rz
+            if hi > k * h and lo < (k + 1) * h:
+                touching.append(ob)
+        if not touching:
+            continue
+        pts = np.ones((sub, ny * sub, nx * sub), dtype=np.float64)
+        for ob in touching:
+            if isinstance(ob, Box):
+                ix = np.nonzero((xs >= ob.x0) & (xs < ob.x1))[0]
+                iy = np.nonzero((ys >= ob.y0) & (ys < ob.y1))[0]
+                iz = np.nonzero((zs >= ob.z0) & (zs < ob.z1))[0]
+                if len(ix) == 0 or len(iy) == 0 or len(iz) == 0:
+                    continue
+                sl = pts[iz[0]:iz[-1] + 1, iy[0]:iy[-1] + 1, ix[0]:ix[-1] + 1]
+                np.minimum(sl, ob.phi, out=sl)
+            else:
+                ix = np.nonzero(np.abs(xs - ob.cx) < ob.rx)[0]
+                iy = np.nonzero(np.abs(ys - ob.cy) < ob.ry)[0]
+                if len(ix) == 0 or len(iy) == 0:
+                    continue
+                X = xs[ix[0]:ix[-1] + 1][None, None, :]
+                Y = ys[iy[0]:iy[-1] + 1][None, :, None]
+                Z = zs[:, None, None]
+                inside = (((X - ob.cx) / ob.rx) ** 2 + ((Y - ob.cy) / ob.ry) ** 2
+                          + ((Z - ob.cz) / ob.rz) ** 2) < 1.0
+                sl = pts[:, iy[0]:iy[-1] + 1, ix[0]:ix[-1] + 1]
+                sl[inside] = np.minimum(sl[inside], ob.phi)
+        phi[k] = pts.reshape(sub, ny, sub, nx, sub).mean(axis=(0, 2, 4))
+    return phi
+
+
+def single_box(nx=64, ny=32, nz=16, h=2.0, size=(20.0, 10.0, 12.0), u_ref=5.0,
+               steps=100) -> Scenario:
+    """One solid box (porosity 0) centred in x and y, standing on the ground;
+    uniform inflow on x-, zero-gradient outflow on x+, slip top and sides,
+    no-slip ground."""
+    lx, ly = nx * h, ny * h
+    b = Box(lx / 2 - size[0] / 2, lx / 2 + size[0] / 2, ly / 2 - size[1] / 2,
+            ly / 2 + size[1] / 2, 0.0, size[2], 0.0)
+    phi = rasterize(nx, ny, nz, h, [b])
+    return Scenario(nx, ny, nz, h, phi, wind_dir_deg=0.0, u_ref=u_ref, inflow_loglaw=False,
+                    ground_noslip=True, steps=steps, name=f"single_box_{nx}x{ny}x{nz}",
+                    objects=[b])
+
+
+def urban_block(nx=256, ny=256, nz=64, h=2.0, n_boxes=40, n_trees=60, seed=0,
+                footprint=(10.0, 40.0), height=(10.0, 60.0), radius=(3.0, 8.0),
+                tree_phi=(0.3, 0.8), trunk=(2.0, 5.0), u_ref=3.0, wind_dir_deg=0.0,
+                margin=0.10, steps=500) -> Scenario:
+    """Seeded urban block: axis-aligned solid boxes plus porous ellipsoidal
+    canopies, log-law inflow.
+
+    Draw order per box: x-extent, y-extent, height, centre x, centre y.
+    Per canopy: radius, porosity, trunk height, centre x, centre y.
+    Objects keep a margin (fraction of the domain length) from the four
+    lateral sides, so inflow and outflow faces stay clear.
+    """
+    rng = SplitMix64(seed)
+    lx, ly, lz = nx * h, ny * h, nz * h
+    mx, my = margin * lx, margin * ly
+    objects = []
+    for _ in range(n_boxes):
+        sx = rng.uniform(*footprint)
+        sy = rng.uniform(*footprint)
+        hz = min(rng.uniform(*height), lz - h)
+        cx = rng.uniform(mx + sx / 2, lx - mx - sx / 2)
+        cy = rng.uniform(my + sy / 2, ly - my - sy / 2)
+        objects.append(Box(cx - sx / 2, cx + sx / 2, cy - sy / 2, cy + sy / 2, 0.0, hz, 0.0))
+    for _ in range(n_trees):
+        r = rng.uniform(*radius)
+        ph = rng.uniform(*tree_phi)
+        tz = rng.uniform(*trunk)
+        cx = rng.uniform(mx + r, lx - mx - r)
+        cy = rng.uniform(my + r, ly - my - r)
+        objects.append(Ellipsoid(cx, cy, 0.75 * r + tz, r, r, 0.75 * r, ph))
+    phi = rasterize(nx, ny, nz, h, objects)
+    return Scenario(nx, ny, nz, h, phi, wind_dir_deg=wind_dir_deg, u_ref=u_ref,
+                    z_ref=10.0, z0=0.5, inflow_loglaw=True, ground_noslip=True, steps=steps,
+                    name=f"urban_{nx}x{ny}x{nz}_s{seed}", objects=objects)
+
+
+def scaled_urban_block(nx, ny, nz, h=2.0, seed=0, wind_dir_deg=0.0, u_ref=3.0, steps=300,
+                       ref_cells_xy=256 * 256, ref_boxes=40, ref_trees=60) -> Scenario:
+    """Urban block whose object counts scale with the footprint area."""
+    area = nx * ny / ref_cells_xy
+    nb = max(1, int(round(ref_boxes * area)))
+    nt = max(1, int(round(ref_trees * area)))
+    return urban_block(nx, ny, nz, h, n_boxes=nb, n_trees=nt, seed=seed, u_ref=u_ref,
+                       wind_dir_deg=wind_dir_deg, steps=steps)
+
+
+def empty_domain(nx, ny, nz, h=1.0, u_ref=2.0, wind_dir_deg=0.0, ground_noslip=False,
+                 loglaw=False) -> Scenario:
+    phi = np.ones((nz, ny, nx))
+    return Scenario(nx, ny, nz, h, phi, wind_dir_deg=wind_dir_deg, u_ref=u_ref,
+                    inflow_loglaw=loglaw, ground_noslip=ground_noslip, name="empty")
+
+
+def random_fields(nx, ny, nz, seed=0, scale=1.0) -> dict:
+    """Seeded random velocity / turbulence fields for operator-level tests."""
+    g = np.random.default_rng(seed)
+    return {
+        "u": scale * g.standard_normal((nz, ny, nx + 1)),
+        "v": scale * g.standard_normal((nz, ny + 1, nx)),
+        "w": scale * g.standard_normal((nz + 1, ny, nx)),
+        "p": g.standard_normal((nz, ny, nx)),
+        "k": 0.1 + 0.5 * g.random((nz, ny, nx)),
+        "omega": 0.05 + 0.5 * g.random((nz, ny, nx)),
+    }
+
+
+def batch_instances(n=32, seed=0, sizes_xy=(96, 256), sizes_z=(32, 64), speed=(2.0, 8.0),
+                    steps=300):
+    """Instances of uneven size, wind direction and speed for the batched run.
+
+    Per instance, in order: nx, ny (multiples of 16), nz (multiple of 8),
+    wind direction in [0, 360), speed, layout seed.
+    """
+    rng = SplitMix64(seed)
+    out = []
+    for _ in range(n):
+        nx = 16 * rng.randint(sizes_xy[0] // 16, sizes_xy[1] // 16)
+        ny = 16 * rng.randint(sizes_xy[0] // 16, sizes_xy[1] // 16)
+        nz = 8 * rng.randint(sizes_z[0] // 8, sizes_z[1] // 8)
+        wd = rng.uniform(0.0, 360.0)
+        sp = rng.uniform(*speed)
+        s = rng.next_u64() & 0xFFFFFFFF
+        sc = scaled_urban_block(nx, ny, nz, seed=s, wind_dir_deg=wd, u_ref=sp, steps=steps)
+        out.append(sc)
+    return out
+
+
+def config(name: str) -> Scenario:
+    """Named workloads: the five configurations of the benchmark plan."""
+    if name == "single_box":      # 64x32x16, FP64, 100 steps
+        return single_box()
+    if name == "urban256":        # 256x256x64, FP32 + FP64 reductions, 500 steps
+        return urban_block()
+    if name == "urban512":        # 512x512x128, 1 m cells
+        return urban_block(512, 512, 128, h=1.0, n_boxes=400, n_trees=800,
+                           height=(5.0, 120.0), u_ref=5.0, steps=1000)
+    raise KeyError(name)
+
+
+def angle_is_axis(deg: float) -> bool:
+    return abs(math.sin(math.radians(deg))) < 1e-9 or abs(math.cos(math.radians(deg))) < 1e-9
