@@ -1,0 +1,208 @@
+/*
+ * uf.h -- C ABI of the GB300-native UrbanFlow RANS step.
+ *
+ * The library advances the Reynolds-averaged Navier-Stokes equations with a
+ * k-omega closure and a porosity drag on a uniform staggered 3D grid, as in
+ * "UrbanFlow: Designing Comfortable Outdoor Areas" (arXiv 2204.01117), Sec. 3:
+ *   momentum      : Eq. (momen_drag), RANS with eddy viscosity and drag f_d
+ *   drag          : Sec. 3 footnote + forward-Euler drag equation,
+ *                   u <- max(0, 1 - dt C_d a ((1-phi)/(phi+e))^b |u|) u
+ *   turbulence    : k and omega equations, P_k, nu_t = k / omega~ (Sec. 3),
+ *                   Table 1 coefficients, viscosity limiter (Sec. 3)
+ *   discretisation: staggered MAC grid, operator splitting, MacCormack
+ *                   semi-Lagrangian advection, pressure Poisson projection
+ *                   solved by preconditioned CG (Sec. 3, App. A.3)
+ *   boundaries    : inlet Dirichlet, outlet zero normal derivative, walls,
+ *                   outlet pressure 0, dp/dn = 0 elsewhere (Sec. 3)
+ *
+ * Conventions shared by every entry point:
+ *   - All functions return a uf_status and never throw or abort.  On failure
+ *     uf_last_error() returns a message for the calling thread.
+ *   - Device memory is owned by the caller.  The library never calls
+ *     cudaMalloc or cudaFree: the caller allocates one workspace of
+ *     uf_workspace_bytes() bytes (any device allocator; 256-byte aligned) and
+ *     keeps it alive until uf_destroy().  The library owns only small host-side
+ *     objects (the grid handle, CUDA graphs, one internal capture stream).
+ *   - Work is enqueued on the CUDA stream given at creation and is
+ *     asynchronous unless a stats pointer is passed.
+ *   - Field buffers exchanged through uf_set_state / uf_get_state /
+ *     uf_set_porosity are dense arrays, x fastest then y then z, in the grid's
+ *     precision (float for UF_F32, double for UF_F64).  They may live in host
+ *     memory (pageable or pinned) or device memory; the copy direction is
+ *     inferred from the pointer.
+ *   - Field extents: u (nx+1)*ny*nz, v nx*(ny+1)*nz, w nx*ny*(nz+1);
+ *     p, k, omega, phi, nu_t nx*ny*nz.
+ */
+#ifndef UF_H
+#define UF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct uf_grid uf_grid;
+
+typedef enum {
+  UF_OK = 0,
+  UF_ERR_ARG = 1,            /* invalid argument or description            */
+  UF_ERR_CUDA = 2,           /* a CUDA runtime call failed                  */
+  UF_ERR_NOMEM = 3,          /* workspace too small                         */
+  UF_ERR_NOT_CONVERGED = 4,  /* pressure CG hit its iteration cap           */
+  UF_ERR_NAN = 5,            /* non-finite residual in the pressure solve   */
+  UF_ERR_TIMEOUT = 6,        /* a bounded device wait gave up               */
+  UF_ERR_STATE = 7           /* call out of order (e.g. step before init)   */
+} uf_status;
+
+enum { UF_F32 = 0,   /* FP32 fields, FP64 reductions and coarsest MG solve */
+       UF_F64 = 1 }; /* FP64 throughout                                     */
+
+enum { UF_PRECOND_MG = 0,      /* geometric multigrid V-cycle (default)       */
+       UF_PRECOND_AI1 = 1,     /* approximate inverse, 1st order (Sec. 3)     */
+       UF_PRECOND_JACOBI = 2,
+       UF_PRECOND_NONE = 3 };
+
+enum { UF_FIELD_U = 0, UF_FIELD_V = 1, UF_FIELD_W = 2, UF_FIELD_P = 3,
+       UF_FIELD_K = 4, UF_FIELD_OMEGA = 5, UF_FIELD_PHI = 6, UF_FIELD_NUT = 7 };
+
+/* Grid and physics description.  uf_default_desc() fills the paper's
+ * constants: Table 1 (C_mu 0.09, alpha 0.52, beta 0.0708, sigma 0.5,
+ * sigma* 0.6, C_lim 7/8), drag a = 0.62, b = 2.5, e = 1e-10 (Sec. 3
+ * footnote), C_d = 1.0 (App. A.2), and the readings of what the paper leaves
+ * open: rho = 1.225 kg/m^3, nu = 1.5e-5 m^2/s, I = 0.1, L = 10 m, CFL 0.5,
+ * k >= 1e-10, omega >= 1e-6, CG stop ||r|| <= 1e-7 ||b|| (FP32) or 1e-12
+ * (FP64) when cg_tol is 0 (the default), at most 200 iterations, AI relaxation w = 1.65 (App. A.3: best
+ * w lies in 1.6-1.7). */
+typedef struct {
+  int nx, ny, nz;          /* cells; nx, ny >= 2, nz >= 1                   */
+  double h;                /* cell size [m]                                 */
+  int precision;           /* UF_F32 or UF_F64                              */
+  double wind_dir_deg;     /* horizontal wind direction, 0 = +x, 90 = +y     */
+  double u_ref;            /* inflow speed [m/s] (at z_ref for the log law)  */
+  double z_ref, z0;        /* log-law reference height and roughness [m]    */
+  int inflow_loglaw;       /* 0: uniform u_ref; 1: log law (Sec. 6.1)       */
+  int ground_noslip;       /* 1: no-slip ground; 0: slip ground             */
+  double rho, nu, Cd, a, b, e;
+  double I, L;             /* inlet turbulence intensity and length scale   */
+  double C_mu, alpha, beta, sigma, sigma_star, C_lim;
+  double cfl;              /* dt = cfl h / max|u| unless fixed_dt > 0       */
+  double fixed_dt;
+  double k_min, omega_min;
+  int precond;             /* UF_PRECOND_*                                   */
+  double cg_tol;           /* ||r||/||b|| to stop at; 0 = by precision      */
+  int cg_max_iter;
+  double ai_omega;         /* relaxation of the AI preconditioner           */
+  double mg_jacobi_omega;  /* damping of the MG Jacobi smoother (6/7)       */
+  int mg_coarse_max;       /* coarsest MG level has at most this many cells */
+  int mg_smoother;         /* UF_SMOOTH_JACOBI (default) or UF_SMOOTH_RBGS  */
+} uf_grid_desc;
+
+enum { UF_SMOOTH_JACOBI = 0,   /* damped Jacobi, 2 sweeps before + 2 after        */
+       UF_SMOOTH_RBGS = 1 };   /* red-black Gauss-Seidel, red-black / black-red   */
+
+typedef struct {
+  double dt;               /* time step taken                                */
+  int cg_iters;            /* CG iterations of the pressure solve            */
+  double cg_rel_residual;  /* ||r||/||b|| at exit (recursive residual)      */
+  int status;              /* uf_status of the device-side checks           */
+} uf_step_stats;
+
+/* Per-kernel timing of one profiled step (uf_profile_step). */
+typedef struct {
+  char name[40];           /* kernel label, e.g. "cg_direction_spmv"         */
+  int launches;            /* launches in the profiled step                  */
+  double total_ms;         /* summed CUDA-event time of those launches      */
+  double bytes_per_launch; /* algorithmic HBM bytes one launch must move    */
+} uf_kernel_time;
+
+/* Fills *d with the paper's constants and the stated readings (see above);
+ * sizes default to 64 x 32 x 16, h = 2 m, 5 m/s uniform inflow along +x. */
+void uf_default_desc(uf_grid_desc* d);
+
+/* Bytes of device workspace the grid needs (0 if the description is
+ * invalid).  The value includes 256 bytes of alignment slack. */
+size_t uf_workspace_bytes(const uf_grid_desc* d);
+
+/* Creates a grid on the current CUDA device.  d_workspace: device pointer to
+ * at least uf_workspace_bytes(d) bytes, owned by the caller.  stream: a
+ * cudaStream_t (NULL = legacy default stream is rejected; pass a created
+ * stream).  The workspace is zeroed; porosity defaults to 1 (open air) and
+ * the state to zero until uf_set_state or uf_init_state.
+ * Errors: UF_ERR_ARG (bad description or NULL pointers), UF_ERR_NOMEM (bytes
+ * too small), UF_ERR_CUDA. */
+uf_status uf_create_grid(const uf_grid_desc* d, void* d_workspace, size_t bytes, void* stream, uf_grid** out);
+
+/* Releases host-side objects and graphs; the workspace stays the caller's. */
+uf_status uf_destroy(uf_grid* g);
+
+/* Sets the porosity field phi (nx*ny*nz values in [0,1], grid precision,
+ * host or device pointer) and derives the per-cell drag coefficient
+ * C_d a ((1-phi)/(phi+e))^b (Sec. 3 footnote). */
+uf_status uf_set_porosity(uf_grid* g, const void* phi);
+
+/* Copies one field (UF_FIELD_*) in or out, dense layout, grid precision.
+ * Setting U, V or W expects every face, boundary faces included. */
+uf_status uf_set_state(uf_grid* g, int field, const void* buf);
+uf_status uf_get_state(uf_grid* g, int field, void* buf);
+
+/* Initial state: the inflow profile on every face (Dirichlet values on the
+ * boundary faces), k and omega at the inlet values of Sec. 3
+ * (k = 1.5 (I U)^2, omega = k^1/2 / (C_mu^1/4 L)), one drag step with the
+ * CFL time step, the BCs, and one pressure projection from p = 0. */
+uf_status uf_init_state(uf_grid* g);
+
+/* One time step: dt -> eddy viscosity -> MacCormack advection -> diffusion
+ * -> drag + velocity BCs -> pressure solve (warm start from the previous
+ * pressure) -> projection -> k-omega update.  Replays a captured CUDA graph;
+ * the CG loop runs in a conditional (while) graph node, so the host never
+ * waits inside the step.  stats == NULL: asynchronous.  stats != NULL: the
+ * call synchronises the stream and fills *stats; a failed device check is
+ * returned (UF_ERR_NOT_CONVERGED, UF_ERR_NAN). */
+uf_status uf_step(uf_grid* g, uf_step_stats* stats);
+
+/* nsteps calls of uf_step; stats (may be NULL) describe the last step and,
+ * when given, the call synchronises and reports the first device error of
+ * any of the steps. */
+uf_status uf_run(uf_grid* g, int nsteps, uf_step_stats* last);
+
+/* Pedestrian-level comfort objective on the current state: over cells whose
+ * centre height lies in [z_lo, z_hi], the sum of max(|u_c| - u_hi, 0)^2 +
+ * max(u_lo - |u_c|, 0)^2 with the cell-centre velocity averaged from the
+ * faces; FP64 accumulation.  Synchronises. */
+uf_status uf_objective(uf_grid* g, double z_lo, double z_hi, double u_hi, double u_lo, double* J_out);
+
+/* Divergence diagnostic ||h div u||_2 / ||u_cell||_2 of the current
+ * velocity.  Synchronises. */
+uf_status uf_divergence(uf_grid* g, double* out);
+
+/* Applies the pressure operator A (matrix-free 7-point, BC aware) to a cell
+ * field x (device pointer, grid precision, dense) into y.  Synchronises. */
+uf_status uf_apply_poisson(uf_grid* g, const void* x, void* y);
+
+/* Solves A p = b with the grid's preconditioned CG starting from the grid's
+ * current pressure; b is a dense cell field (host or device).  The result
+ * replaces the grid's pressure.  Synchronises; fills iterations and the
+ * final relative residual. */
+uf_status uf_poisson_solve(uf_grid* g, const void* b, int* iters, double* rel_residual);
+
+/* One time step computed by the same kernels as uf_step, but launched one
+ * by one on the grid's stream with a CUDA event pair around every launch and
+ * the CG loop polled from the host (the step advances the state exactly like
+ * uf_step).  Writes up to `capacity` entries, one per kernel label, and the
+ * number of labels to *count.  Synchronises.  Used to measure kernel
+ * durations and for per-kernel profilers, which cannot see inside graphs that
+ * hold conditional nodes. */
+uf_status uf_profile_step(uf_grid* g, uf_kernel_time* out, int capacity, int* count, uf_step_stats* stats);
+
+/* Kernel launches per step of the captured graph, counting every CG
+ * iteration of the last step; 0 before the first step. */
+int uf_last_step_launches(uf_grid* g);
+
+/* Thread-local message of the last failure. */
+const char* uf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UF_H */

@@ -1,0 +1,1046 @@
+// Host side of the UrbanFlow RANS step: workspace layout, multigrid
+// hierarchy, CUDA-graph capture and the C ABI declared in include/uf.h.
+//
+// One uf_step replays a CUDA graph captured once per grid (two graphs, one per
+// parity of the k/omega ping-pong buffers).  The pressure CG loop sits in a
+// conditional WHILE node whose body is {direction + SpMV, update + norm,
+// preconditioner}; the update kernel clears the condition when
+// ||r|| <= tol ||b||, when the iteration cap is hit or when the residual is not
+// finite, so the host never polls inside a step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/uf.h"
+#include "mg_fused.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+uf_status fail(uf_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define UF_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(UF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+int pitch_of(int lx) { return (int)round_up((size_t)lx, 32); }
+
+constexpr int kPartials = 8192;      // doubles per partials buffer
+constexpr int kDtBlocks = 1024;
+constexpr int kTargetBlocks = 2048;  // blocks of reducing cell kernels
+constexpr size_t kTailSmemBudget = 200 * 1024;
+
+struct LevelDims {
+  int nx, ny, nz, P;
+  int fx, fy, fz;   // coarsening factor relative to the finest level
+  int cx, cy, cz;   // the next level halves this axis
+};
+
+std::vector<LevelDims> mg_hierarchy(int nx, int ny, int nz, int coarse_max) {
+  std::vector<LevelDims> L;
+  LevelDims d{nx, ny, nz, pitch_of(nx), 1, 1, 1, 0, 0, 0};
+  L.push_back(d);
+  while (L.size() < 16) {
+    LevelDims& f = L.back();
+    if (f.nx < 2 && f.ny < 2 && f.nz < 2) break;
+    if (L.size() > 1 && (long)f.nx * f.ny * f.nz <= coarse_max) break;
+    f.cx = f.nx >= 2; f.cy = f.ny >= 2; f.cz = f.nz >= 2;
+    LevelDims c{f.cx ? (f.nx + 1) / 2 : f.nx, f.cy ? (f.ny + 1) / 2 : f.ny, f.cz ? (f.nz + 1) / 2 : f.nz, 0,
+                f.fx * (f.cx ? 2 : 1), f.fy * (f.cy ? 2 : 1), f.fz * (f.cz ? 2 : 1), 0, 0, 0};
+    c.P = pitch_of(c.nx);
+    L.push_back(c);
+  }
+  return L;
+}
+
+// Workspace layout: every buffer 256-byte aligned.
+struct Layout {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off += round_up(bytes, 256);
+    return o;
+  }
+};
+
+bool desc_valid(const uf_grid_desc* d, std::string* why) {
+  if (!d) { *why = "NULL description"; return false; }
+  if (d->nx < 2 || d->ny < 2 || d->nz < 1) { *why = "need nx, ny >= 2 and nz >= 1"; return false; }
+  if ((long long)d->nx * d->ny * d->nz > (1LL << 31)) { *why = "grid too large"; return false; }
+  if (!(d->h > 0)) { *why = "h must be positive"; return false; }
+  // every reducing launch keeps at most kPartials blocks (one 32 x 8 tile each)
+  if ((long long)((d->nx + 32) / 32) * ((d->ny + 8) / 8) > kPartials / 2) { *why = "nx * ny too large"; return false; }
+  if (d->precision != UF_F32 && d->precision != UF_F64) { *why = "precision must be UF_F32 or UF_F64"; return false; }
+  if (!(d->u_ref >= 0) || (d->u_ref == 0 && !(d->fixed_dt > 0))) { *why = "u_ref must be > 0 (or fixed_dt > 0)"; return false; }
+  if (d->inflow_loglaw && !(d->z0 > 0 && d->z_ref > d->z0)) { *why = "log law needs z_ref > z0 > 0"; return false; }
+  if (d->precond < UF_PRECOND_MG || d->precond > UF_PRECOND_NONE) { *why = "unknown preconditioner"; return false; }
+  if (!(d->cg_tol >= 0) || d->cg_max_iter < 1) { *why = "cg_tol >= 0 and cg_max_iter >= 1 required"; return false; }
+  if (d->mg_smoother != UF_SMOOTH_JACOBI && d->mg_smoother != UF_SMOOTH_RBGS) { *why = "unknown smoother"; return false; }
+  if (!(d->ai_omega > 0 && d->ai_omega < 2)) { *why = "ai_omega must lie in (0, 2)"; return false; }
+  if (!(d->mg_jacobi_omega > 0 && d->mg_jacobi_omega <= 1)) { *why = "mg_jacobi_omega must lie in (0, 1]"; return false; }
+  if (d->mg_coarse_max < 1 || d->mg_coarse_max > 1024) { *why = "mg_coarse_max must lie in [1, 1024]"; return false; }
+  if (!(d->cfl > 0) && !(d->fixed_dt > 0)) { *why = "cfl or fixed_dt must be positive"; return false; }
+  // at least one outlet side, otherwise the pressure operator is singular
+  const double th = d->wind_dir_deg * M_PI / 180.0;
+  const double cx = std::cos(th), sy = std::sin(th);
+  if (!(cx < -1e-9 || cx > 1e-9 || sy < -1e-9 || sy > 1e-9)) { *why = "wind direction undefined"; return false; }
+  return true;
+}
+
+// Host-side summary of a grid's buffers (offsets into the workspace).
+struct Plan {
+  int T_bytes;
+  int nx, ny, nz, Pu, Pc;
+  size_t n_u, n_v, n_w, n_c;   // padded element counts
+  std::vector<LevelDims> levels;
+  int coarse_n;
+  // offsets
+  size_t u, v, w, uh, vh, wh, ut, vt, wt, k0, k1, o0, o1, cc, phi, nut, p, b, r, r2, z, q, d0, d1;
+  int tail_level;          // first level run by the shared-memory tail kernel
+  size_t tail_smem;        // its dynamic shared memory (bytes)
+  std::vector<int> tail_off;
+  std::vector<size_t> lr, lx, lt;
+  size_t prof, dt, scal, state, partials, ainv;
+  size_t total;
+};
+
+Plan make_plan(const uf_grid_desc* d) {
+  Plan P;
+  P.T_bytes = d->precision == UF_F64 ? 8 : 4;
+  P.nx = d->nx; P.ny = d->ny; P.nz = d->nz;
+  P.Pu = pitch_of(d->nx + 1);
+  P.Pc = pitch_of(d->nx);
+  P.n_u = (size_t)P.Pu * d->ny * d->nz;
+  P.n_v = (size_t)P.Pc * (d->ny + 1) * d->nz;
+  P.n_w = (size_t)P.Pc * d->ny * (d->nz + 1);
+  P.n_c = (size_t)P.Pc * d->ny * d->nz;
+  Layout L;
+  const size_t tb = P.T_bytes;
+  P.u = L.take(P.n_u * tb); P.v = L.take(P.n_v * tb); P.w = L.take(P.n_w * tb);
+  P.uh = L.take(P.n_u * tb); P.vh = L.take(P.n_v * tb); P.wh = L.take(P.n_w * tb);
+  P.ut = L.take(P.n_u * tb); P.vt = L.take(P.n_v * tb); P.wt = L.take(P.n_w * tb);
+  P.k0 = L.take(P.n_c * tb); P.k1 = L.take(P.n_c * tb);
+  P.o0 = L.take(P.n_c * tb); P.o1 = L.take(P.n_c * tb);
+  P.cc = L.take(P.n_c * tb); P.phi = L.take(P.n_c * tb); P.nut = L.take(P.n_c * tb);
+  P.p = L.take(P.n_c * tb); P.b = L.take(P.n_c * tb); P.r = L.take(P.n_c * tb);
+  P.r2 = L.take(P.n_c * tb);
+  P.z = L.take(P.n_c * tb); P.q = L.take(P.n_c * tb);
+  P.d0 = L.take(P.n_c * tb); P.d1 = L.take(P.n_c * tb);
+  P.levels = mg_hierarchy(d->nx, d->ny, d->nz, d->mg_coarse_max);
+  const bool mg = d->precond == UF_PRECOND_MG;
+  const size_t nl = mg ? P.levels.size() : 1;
+  P.lr.assign(nl, 0); P.lx.assign(nl, 0); P.lt.assign(nl, 0);
+  for (size_t l = 0; l < nl; ++l) {
+    const LevelDims& ld = P.levels[l];
+    const size_t n = (size_t)ld.P * ld.ny * ld.nz;
+    P.lr[l] = l == 0 ? P.r : L.take(n * tb);
+    P.lx[l] = L.take(n * tb);
+    P.lt[l] = L.take(n * tb);
+  }
+  const LevelDims& cl = P.levels.back();
+  P.coarse_n = mg ? cl.nx * cl.ny * cl.nz : 0;
+  // tail: deepest suffix of levels (never the finest) whose three bordered
+  // arrays per level fit the shared-memory budget
+  P.tail_level = (int)nl - 1;
+  auto bordered = [&](int m) {
+    return (size_t)(P.levels[m].nx + 2) * (P.levels[m].ny + 2) * (P.levels[m].nz + 2);
+  };
+  if (mg) {
+    for (int l = (int)nl - 1; l >= 1; --l) {
+      size_t bytes = 0;
+      for (int m = l; m < (int)nl; ++m) bytes += 3 * bordered(m) * tb;
+      if (bytes > kTailSmemBudget) break;
+      P.tail_level = l;
+    }
+    P.tail_off.assign(nl, 0);
+    size_t off = 0;
+    for (int m = P.tail_level; m < (int)nl; ++m) {
+      P.tail_off[m] = (int)off;
+      off += 3 * bordered(m);
+    }
+    P.tail_smem = off * tb;
+  } else {
+    P.tail_smem = 0;
+  }
+  P.prof = L.take((size_t)d->nz * tb);
+  P.dt = L.take(8);
+  P.scal = L.take(8 * 8);
+  P.state = L.take(sizeof(uf::SolveState));
+  P.partials = L.take(sizeof(double) * kPartials * 2);
+  P.ainv = L.take(sizeof(double) * (size_t)P.coarse_n * P.coarse_n);
+  P.total = L.off + 256;
+  return P;
+}
+
+// Dense operator of a level (compact order i + nx (j + ny k)).
+std::vector<double> dense_level_operator(const LevelDims& ld, double wx, double wy, double wz, int out_mask) {
+  const int n = ld.nx * ld.ny * ld.nz;
+  std::vector<double> A((size_t)n * n, 0.0);
+  auto id = [&](int i, int j, int k) { return i + ld.nx * (j + ld.ny * k); };
+  for (int k = 0; k < ld.nz; ++k)
+    for (int j = 0; j < ld.ny; ++j)
+      for (int i = 0; i < ld.nx; ++i) {
+        const int c = id(i, j, k);
+        auto face = [&](bool in, int m, double w, int bit) {
+          if (in) { A[(size_t)c * n + c] += w; A[(size_t)c * n + m] -= w; }
+          else if (out_mask & bit) A[(size_t)c * n + c] += w;
+        };
+        face(i > 0, i > 0 ? id(i - 1, j, k) : 0, wx, 1);
+        face(i < ld.nx - 1, i < ld.nx - 1 ? id(i + 1, j, k) : 0, wx, 2);
+        face(j > 0, j > 0 ? id(i, j - 1, k) : 0, wy, 4);
+        face(j < ld.ny - 1, j < ld.ny - 1 ? id(i, j + 1, k) : 0, wy, 8);
+        face(k > 0, k > 0 ? id(i, j, k - 1) : 0, wz, 16);
+        face(k < ld.nz - 1, k < ld.nz - 1 ? id(i, j, k + 1) : 0, wz, 32);
+      }
+  return A;
+}
+
+// Inverse of an SPD matrix by Cholesky factorisation (FP64).
+bool spd_inverse(std::vector<double>& A, int n, std::vector<double>& inv) {
+  std::vector<double> Lm((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double s = A[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) s -= Lm[(size_t)j * n + k] * Lm[(size_t)j * n + k];
+    if (!(s > 0)) return false;
+    const double ljj = std::sqrt(s);
+    Lm[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double t = A[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) t -= Lm[(size_t)i * n + k] * Lm[(size_t)j * n + k];
+      Lm[(size_t)i * n + j] = t / ljj;
+    }
+  }
+  inv.assign((size_t)n * n, 0.0);
+  std::vector<double> y(n);
+  for (int col = 0; col < n; ++col) {
+    for (int i = 0; i < n; ++i) {   // L y = e_col
+      double t = (i == col) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) t -= Lm[(size_t)i * n + k] * y[k];
+      y[i] = t / Lm[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {   // L^T x = y
+      double t = y[i];
+      for (int k = i + 1; k < n; ++k) t -= Lm[(size_t)k * n + i] * inv[(size_t)k * n + col];
+      inv[(size_t)i * n + col] = t / Lm[(size_t)i * n + i];
+    }
+  }
+  return true;
+}
+
+double inflow_speed(const uf_grid_desc& d, double z) {
+  if (!d.inflow_loglaw) return d.u_ref;
+  const double kappa = 0.41;
+  const double ustar = d.u_ref * kappa / std::log(d.z_ref / d.z0);
+  const double s = ustar / kappa * std::log(z / d.z0);
+  return s > 0.0 ? s : 0.0;
+}
+
+dim3 plane_grid(int lx, int ly, int planes) {
+  return dim3((lx + uf::BX - 1) / uf::BX, (ly + uf::BY - 1) / uf::BY, planes);
+}
+
+// z-chunking of a cell kernel: returns the grid and the planes per block.
+dim3 chunk_grid(int lx, int ly, int lz, int* zc) {
+  const int gx = (lx + uf::BX - 1) / uf::BX, gy = (ly + uf::BY - 1) / uf::BY;
+  int chunks = std::max(1, std::min(lz, kTargetBlocks / std::max(1, gx * gy)));
+  *zc = (lz + chunks - 1) / chunks;
+  chunks = (lz + *zc - 1) / *zc;
+  return dim3(gx, gy, chunks);
+}
+
+}  // namespace
+
+// ======================================================================
+struct uf_grid {
+  virtual ~uf_grid() {}
+  virtual uf_status set_porosity(const void*) = 0;
+  virtual uf_status set_state(int, const void*) = 0;
+  virtual uf_status get_state(int, void*) = 0;
+  virtual uf_status init_state() = 0;
+  virtual uf_status step(uf_step_stats*) = 0;
+  virtual uf_status run(int, uf_step_stats*) = 0;
+  virtual uf_status objective(double, double, double, double, double*) = 0;
+  virtual uf_status divergence(double*) = 0;
+  virtual uf_status apply_poisson(const void*, void*) = 0;
+  virtual uf_status poisson_solve(const void*, int*, double*) = 0;
+  virtual int last_launches() = 0;
+  virtual uf_status profile_step(uf_kernel_time*, int, int*, uf_step_stats*) = 0;
+};
+
+namespace {
+
+template <typename T>
+class GridImpl final : public uf_grid {
+ public:
+  uf_grid_desc d;
+  Plan P;
+  char* ws = nullptr;
+  cudaStream_t stream = nullptr, cap = nullptr, cap2 = nullptr;
+  uf::StepParams<T> sp;
+  std::vector<uf::Level<T>> lv;
+  T *u, *v, *w, *uh, *vh, *wh, *ut, *vt, *wt, *kb[2], *ob[2], *cc, *phi, *nut, *p, *b, *r, *r2, *z, *q, *d0, *d1, *prof;
+  uf::TailArgs<T> tail;
+  double *dt, *scal, *partials, *ainv;
+  uf::SolveState* st;
+  cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
+  cudaGraphExec_t init_exec = nullptr, solve_exec = nullptr;
+  int parity = 0;
+  bool have_state = false;
+  int launches_fixed = 0, launches_per_iter = 0, launches_solve_setup = 0, last_iters = -1;
+
+  ~GridImpl() override {
+    for (auto& e : step_exec) if (e) cudaGraphExecDestroy(e);
+    for (auto& e : pool) cudaEventDestroy(e);
+    if (init_exec) cudaGraphExecDestroy(init_exec);
+    if (solve_exec) cudaGraphExecDestroy(solve_exec);
+    if (cap) cudaStreamDestroy(cap);
+    if (cap2) cudaStreamDestroy(cap2);
+  }
+
+  template <typename U>
+  U* at(size_t off) { return reinterpret_cast<U*>(ws + off); }
+
+  uf_status setup(const uf_grid_desc* desc, void* workspace, cudaStream_t s) {
+    d = *desc;
+    P = make_plan(desc);
+    ws = reinterpret_cast<char*>(round_up(reinterpret_cast<size_t>(workspace), 256));
+    stream = s;
+    UF_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    UF_CUDA(cudaStreamCreateWithFlags(&cap2, cudaStreamNonBlocking));
+    u = at<T>(P.u); v = at<T>(P.v); w = at<T>(P.w);
+    uh = at<T>(P.uh); vh = at<T>(P.vh); wh = at<T>(P.wh);
+    ut = at<T>(P.ut); vt = at<T>(P.vt); wt = at<T>(P.wt);
+    kb[0] = at<T>(P.k0); kb[1] = at<T>(P.k1); ob[0] = at<T>(P.o0); ob[1] = at<T>(P.o1);
+    cc = at<T>(P.cc); phi = at<T>(P.phi); nut = at<T>(P.nut); p = at<T>(P.p); b = at<T>(P.b);
+    r = at<T>(P.r); r2 = at<T>(P.r2); z = at<T>(P.z); q = at<T>(P.q); d0 = at<T>(P.d0); d1 = at<T>(P.d1);
+    prof = at<T>(P.prof);
+    dt = at<double>(P.dt); scal = at<double>(P.scal); partials = at<double>(P.partials);
+    ainv = at<double>(P.ainv);
+    st = at<uf::SolveState>(P.state);
+    UF_CUDA(cudaMemsetAsync(ws, 0, P.total - 256, stream));
+
+    // physics parameters
+    sp.nx = d.nx; sp.ny = d.ny; sp.nz = d.nz; sp.Pu = P.Pu; sp.Pc = P.Pc;
+    const double th = d.wind_dir_deg * M_PI / 180.0;
+    const double cx = std::cos(th), sy = std::sin(th), tau = 1e-9;
+    const double inward[4] = {cx, -cx, sy, -sy};
+    for (int s2 = 0; s2 < 4; ++s2) sp.side[s2] = inward[s2] > tau ? uf::INFLOW : (inward[s2] < -tau ? uf::OUTFLOW : uf::SLIP);
+    sp.side[4] = d.ground_noslip ? uf::NOSLIP : uf::SLIP;
+    sp.side[5] = uf::SLIP;
+    sp.h = (T)d.h; sp.inv_h = (T)(1.0 / d.h);
+    sp.dirx = (T)cx; sp.diry = (T)sy;
+    sp.rho = (T)d.rho; sp.nu = (T)d.nu;
+    sp.C_mu = (T)d.C_mu; sp.alpha = (T)d.alpha; sp.beta = (T)d.beta; sp.sigma = (T)d.sigma;
+    sp.sigma_star = (T)d.sigma_star; sp.C_lim = (T)d.C_lim;
+    sp.k_min = (T)d.k_min; sp.om_min = (T)d.omega_min;
+    const double uin = inflow_speed(d, d.z_ref);
+    const double kin = 1.5 * (d.I * uin) * (d.I * uin);
+    sp.k_in = (T)kin;
+    sp.om_in = (T)(std::sqrt(kin) / (std::pow(d.C_mu, 0.25) * d.L));
+    sp.prof = prof;
+    sp.dt = dt;
+    std::vector<T> hp(d.nz);
+    for (int k = 0; k < d.nz; ++k) hp[k] = (T)inflow_speed(d, (k + 0.5) * d.h);
+    UF_CUDA(cudaMemcpyAsync(prof, hp.data(), sizeof(T) * d.nz, cudaMemcpyHostToDevice, stream));
+    if (d.fixed_dt > 0) {
+      const double fdt = d.fixed_dt;
+      UF_CUDA(cudaMemcpyAsync(dt, &fdt, sizeof(double), cudaMemcpyHostToDevice, stream));
+    }
+    // solver constants
+    uf::SolveState s0;
+    std::memset(&s0, 0, sizeof(s0));
+    const double tol = d.cg_tol > 0 ? d.cg_tol : (d.precision == UF_F64 ? 1e-12 : 1e-7);
+    s0.tol2 = tol * tol;
+    s0.max_iter = d.cg_max_iter;
+    UF_CUDA(cudaMemcpyAsync(st, &s0, sizeof(s0), cudaMemcpyHostToDevice, stream));
+    // porosity 1 everywhere (open air): drag coefficient 0 (already zeroed)
+    std::vector<T> ones(P.n_c, T(1));
+    UF_CUDA(cudaMemcpyAsync(phi, ones.data(), sizeof(T) * P.n_c, cudaMemcpyHostToDevice, stream));
+
+    // multigrid levels
+    int out_mask = 0;
+    for (int s2 = 0; s2 < 4; ++s2) if (sp.side[s2] == uf::OUTFLOW) out_mask |= 1 << s2;
+    const size_t nl = P.lr.size();
+    lv.resize(nl);
+    for (size_t l = 0; l < nl; ++l) {
+      const LevelDims& ld = P.levels[l];
+      uf::Level<T>& L = lv[l];
+      L.nx = ld.nx; L.ny = ld.ny; L.nz = ld.nz; L.P = ld.P;
+      L.cx = ld.cx; L.cy = ld.cy; L.cz = ld.cz;
+      const double cnt = (double)ld.fx * ld.fy * ld.fz;
+      L.wx = (T)(cnt / ((double)ld.fx * ld.fx));
+      L.wy = (T)(cnt / ((double)ld.fy * ld.fy));
+      L.wz = (T)(cnt / ((double)ld.fz * ld.fz));
+      L.out_mask = out_mask;
+      L.r = at<T>(P.lr[l]); L.x = at<T>(P.lx[l]); L.t = at<T>(P.lt[l]);
+      L.r_alt = nullptr;
+    }
+    if (d.precond == UF_PRECOND_MG) {
+      lv[0].r_alt = r2;
+      std::memset(&tail, 0, sizeof(tail));
+      if (nl > uf::MAX_LEVELS) return fail(UF_ERR_ARG, "too many multigrid levels");
+      for (size_t l = 0; l < nl; ++l) { tail.lv[l] = lv[l]; tail.off[l] = P.tail_off[l]; }
+      tail.lt = P.tail_level;
+      tail.nl = (int)nl;
+      tail.ainv = ainv;
+      tail.n_coarse = P.coarse_n;
+      UF_CUDA(set_smem_limits());
+    }
+    if (d.precond == UF_PRECOND_MG) {
+      const LevelDims& cl = P.levels.back();
+      const uf::Level<T>& L = lv.back();
+      std::vector<double> A = dense_level_operator(cl, (double)L.wx, (double)L.wy, (double)L.wz, out_mask);
+      std::vector<double> inv;
+      if (!spd_inverse(A, P.coarse_n, inv)) return fail(UF_ERR_ARG, "coarsest multigrid operator is not SPD");
+      UF_CUDA(cudaMemcpyAsync(ainv, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice, stream));
+      UF_CUDA(cudaStreamSynchronize(stream));   // host vectors go out of scope
+    } else {
+      UF_CUDA(cudaStreamSynchronize(stream));
+    }
+    return UF_OK;
+  }
+
+  // ------------------------------------------------------------ recording --
+  // Every launch goes through L(): in capture mode it only counts, in the
+  // eager profiling mode it also brackets the launch with CUDA events on the
+  // launching stream.
+  int rec_count = 0;
+  bool profiling = false;
+  struct Rec {
+    std::string name;
+    double bytes;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+
+  cudaEvent_t next_event() {
+    if (pool_used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[pool_used++];
+  }
+  template <typename F>
+  void L(cudaStream_t s, const std::string& name, double bytes, F launch) {
+    rec_count++;
+    if (!profiling) {
+      launch();
+      return;
+    }
+    Rec r{name, bytes, next_event(), next_event()};
+    cudaEventRecord(r.a, s);
+    launch();
+    cudaEventRecord(r.b, s);
+    recs.push_back(r);
+  }
+
+  double N() const { return (double)d.nx * d.ny * d.nz; }
+  double Nl(int l) const { return (double)lv[l].nx * lv[l].ny * lv[l].nz; }
+  double tb() const { return (double)sizeof(T); }
+
+  size_t down_smem() const { return (uf::H2N + uf::H1N + uf::TN) * sizeof(T); }
+  size_t up_smem() const { return (uf::H2N + uf::H1N) * sizeof(T); }
+  size_t dirq_smem() const { return uf::H1N * sizeof(T); }
+
+  cudaError_t set_smem_limits() {
+    cudaError_t e = cudaSuccess;
+    auto lim = [&](const void* f, size_t bytes) {
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    };
+    lim((const void*)uf::k_mg_down<T, uf::SM_JACOBI, true>, down_smem());
+    lim((const void*)uf::k_mg_down<T, uf::SM_JACOBI, false>, down_smem());
+    lim((const void*)uf::k_mg_down<T, uf::SM_RBGS, true>, down_smem());
+    lim((const void*)uf::k_mg_down<T, uf::SM_RBGS, false>, down_smem());
+    lim((const void*)uf::k_mg_up<T, uf::SM_JACOBI, true>, up_smem());
+    lim((const void*)uf::k_mg_up<T, uf::SM_JACOBI, false>, up_smem());
+    lim((const void*)uf::k_mg_up<T, uf::SM_RBGS, true>, up_smem());
+    lim((const void*)uf::k_mg_up<T, uf::SM_RBGS, false>, up_smem());
+    lim((const void*)uf::k_mg_tail<T, uf::SM_JACOBI>, std::max<size_t>(P.tail_smem, 1));
+    lim((const void*)uf::k_mg_tail<T, uf::SM_RBGS>, std::max<size_t>(P.tail_smem, 1));
+    lim((const void*)uf::k_cg_dir_q<T>, dirq_smem());
+    return e;
+  }
+
+  static dim3 tile_grid(const uf::Level<T>& L) {
+    return dim3((L.nx + uf::TX - 1) / uf::TX, (L.ny + uf::TY - 1) / uf::TY, (L.nz + uf::TZ - 1) / uf::TZ);
+  }
+
+  // Fused V-cycle: down kernels to the tail level, the tail, up kernels.
+  // mode 1 (inside the CG loop): the finest down kernel also applies the CG
+  // update and the convergence test.
+  template <int SM>
+  void rec_vcycle_sm(cudaStream_t s, int mode, cudaGraphConditionalHandle cond, int use_cond) {
+    const T om = (T)d.mg_jacobi_omega;
+    const int lt = P.tail_level;
+    for (int l = 0; l < lt; ++l) {
+      const std::string sl = std::to_string(l);
+      const dim3 g = tile_grid(lv[l]);
+      if (l == 0 && mode == 1)
+        L(s, "mg_down_cg_L0", (7 * Nl(0) + Nl(1)) * tb(), [&] {
+          uf::k_mg_down<T, SM, true><<<g, uf::FT, down_smem(), s>>>(lv[0], lv[1], om, p, d0, d1, q, partials, st,
+                                                                   cond, use_cond);
+        });
+      else
+        L(s, "mg_down_L" + sl, (2 * Nl(l) + Nl(l + 1)) * tb(), [&] {
+          uf::k_mg_down<T, SM, false><<<g, uf::FT, down_smem(), s>>>(lv[l], lv[l + 1], om, nullptr, nullptr, nullptr,
+                                                                    nullptr, partials, st, cond, 0);
+        });
+    }
+    L(s, "mg_tail", (double)P.coarse_n * P.coarse_n * 8 + 2 * Nl(lt) * tb(),
+      [&] { uf::k_mg_tail<T, SM><<<1, uf::TAIL_T, P.tail_smem, s>>>(tail, om, st); });
+    for (int l = lt - 1; l >= 0; --l) {
+      const std::string sl = std::to_string(l);
+      const dim3 g = tile_grid(lv[l]);
+      if (l == 0)
+        L(s, "mg_up_L0", (3 * Nl(0) + Nl(1)) * tb(), [&] {
+          uf::k_mg_up<T, SM, true><<<g, uf::FT, up_smem(), s>>>(lv[0], lv[1], om, z, mode, partials, st);
+        });
+      else
+        L(s, "mg_up_L" + sl, (3 * Nl(l) + Nl(l + 1)) * tb(), [&] {
+          uf::k_mg_up<T, SM, false><<<g, uf::FT, up_smem(), s>>>(lv[l], lv[l + 1], om, lv[l].t, mode, partials, st);
+        });
+    }
+  }
+  void rec_vcycle(cudaStream_t s, int mode, cudaGraphConditionalHandle cond, int use_cond) {
+    if (d.mg_smoother == UF_SMOOTH_JACOBI) rec_vcycle_sm<uf::SM_JACOBI>(s, mode, cond, use_cond);
+    else rec_vcycle_sm<uf::SM_RBGS>(s, mode, cond, use_cond);
+  }
+
+  // Non-multigrid preconditioners (one kernel, which also forms r.z).
+  void rec_precond(cudaStream_t s, int mode) {
+    const int kind = d.precond == UF_PRECOND_NONE ? 0 : (d.precond == UF_PRECOND_JACOBI ? 1 : 2);
+    int zc;
+    dim3 g = chunk_grid(lv[0].nx, lv[0].ny, lv[0].nz, &zc);
+    L(s, kind == 2 ? "precond_ai1" : (kind == 1 ? "precond_jacobi" : "precond_copy"), 2 * N() * tb(), [&] {
+      uf::k_precond_simple<T><<<g, dim3(uf::BX, uf::BY), 0, s>>>(lv[0], kind, (T)d.ai_omega, z, zc, mode, partials, st);
+    });
+  }
+
+  void rec_setup_precond(cudaStream_t s) {
+    if (d.precond == UF_PRECOND_MG) rec_vcycle(s, 0, 0, 0);
+    else rec_precond(s, 0);
+  }
+
+  void rec_cg_init(cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
+    int zc;
+    dim3 g = chunk_grid(lv[0].nx, lv[0].ny, lv[0].nz, &zc);
+    L(s, "cg_init", 3 * N() * tb(), [&] {
+      uf::k_cg_init<T><<<g, dim3(uf::BX, uf::BY), 0, s>>>(lv[0], b, p, zc, partials, st, cond, use_cond);
+    });
+  }
+  void rec_cg_iter(cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
+    if (d.precond == UF_PRECOND_MG) {
+      L(s, "cg_dir_q", 4 * N() * tb(), [&] {
+        uf::k_cg_dir_q<T><<<tile_grid(lv[0]), uf::FT, dirq_smem(), s>>>(lv[0], z, d0, d1, q, partials, st);
+      });
+      rec_vcycle(s, 1, cond, use_cond);
+      return;
+    }
+    int zc;
+    dim3 g = chunk_grid(lv[0].nx, lv[0].ny, lv[0].nz, &zc);
+    L(s, "cg_direction_spmv", 4 * N() * tb(), [&] {
+      uf::k_cg_direction_spmv<T><<<g, dim3(uf::BX, uf::BY), 0, s>>>(lv[0], z, d0, d1, q, zc, partials, st);
+    });
+    L(s, "cg_update", 6 * N() * tb(), [&] {
+      uf::k_cg_update<T><<<g, dim3(uf::BX, uf::BY), 0, s>>>(lv[0], p, d0, d1, q, zc, partials, st, cond, use_cond);
+    });
+  }
+
+  // Records the CG solve of A p = b (b, bb and the solver state already set
+  // by the preceding kernel) as set-up kernels + a conditional while node.
+  uf_status rec_solve(cudaStream_t s, cudaGraphConditionalHandle cond, int* setup_count, int* iter_count) {
+    const int before = rec_count;
+    rec_cg_init(s, cond, 1);
+    rec_setup_precond(s);
+    *setup_count = rec_count - before;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cgraph;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    UF_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cgraph, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    UF_CUDA(cudaGraphAddNode(&cnode, cgraph, deps, nullptr, ndeps, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    UF_CUDA(cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    UF_CUDA(cudaStreamBeginCaptureToGraph(cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    const int b2 = rec_count;
+    rec_cg_iter(cap2, cond, 1);
+    if (d.precond != UF_PRECOND_MG) rec_precond(cap2, 1);
+    *iter_count = rec_count - b2;
+    UF_CUDA(cudaStreamEndCapture(cap2, &body));
+    return UF_OK;
+  }
+
+  // The same solve launched eagerly on `s`; the host polls the convergence
+  // flag after every update (profiling mode only).
+  uf_status run_solve_eager(cudaStream_t s) {
+    int conv = 0;
+    rec_cg_init(s, 0, 0);
+    UF_CUDA(cudaMemcpyAsync(&conv, &st->converged, sizeof(int), cudaMemcpyDeviceToHost, s));
+    UF_CUDA(cudaStreamSynchronize(s));
+    if (conv) return UF_OK;
+    rec_setup_precond(s);
+    for (int it = 0; it < d.cg_max_iter + 1; ++it) {
+      rec_cg_iter(s, 0, 0);
+      UF_CUDA(cudaMemcpyAsync(&conv, &st->converged, sizeof(int), cudaMemcpyDeviceToHost, s));
+      UF_CUDA(cudaStreamSynchronize(s));
+      if (conv) break;
+      if (d.precond != UF_PRECOND_MG) rec_precond(s, 1);
+    }
+    return UF_OK;
+  }
+
+  uf::AdvectArgs<T> advect_args() {
+    uf::AdvectArgs<T> A;
+    A.u = u; A.v = v; A.w = w; A.uh = uh; A.vh = vh; A.wh = wh; A.ut = ut; A.vt = vt; A.wt = wt;
+    A.Lu = {d.nx + 1, d.ny, d.nz, P.Pu};
+    A.Lv = {d.nx, d.ny + 1, d.nz, P.Pc};
+    A.Lw = {d.nx, d.ny, d.nz + 1, P.Pc};
+    A.nx = d.nx; A.ny = d.ny; A.nz = d.nz;
+    A.dt = dt;
+    A.inv_h = (T)(1.0 / d.h);
+    return A;
+  }
+
+  void rec_momentum(cudaStream_t s, const T* kin, const T* oin) {
+    const dim3 blk(uf::BX, uf::BY);
+    const double faces = 3 * N() * tb(), cells = N() * tb();
+    if (!(d.fixed_dt > 0))
+      L(s, "cfl_dt", faces, [&] {
+        uf::k_cfl_dt<T><<<kDtBlocks, 256, 0, s>>>(u, P.n_u, v, P.n_v, w, P.n_w, d.cfl * d.h, partials, &st->ticket[0], dt);
+      });
+    L(s, "eddy_viscosity", faces + 3 * cells,
+      [&] { uf::k_eddy_viscosity<T><<<plane_grid(d.nx, d.ny, d.nz), blk, 0, s>>>(sp, u, v, w, kin, oin, nut); });
+    const uf::AdvectArgs<T> A = advect_args();
+    const dim3 ga = plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1);
+    L(s, "advect_forward", 2 * faces, [&] { uf::k_advect_forward<T><<<ga, blk, 0, s>>>(A); });
+    L(s, "advect_backward", 3 * faces, [&] { uf::k_advect_backward<T><<<ga, blk, 0, s>>>(A); });
+    L(s, "diffuse", 2 * faces + cells, [&] { uf::k_diffuse<T><<<ga, blk, 0, s>>>(sp, ut, vt, wt, nut, uh, vh, wh); });
+    L(s, "drag_bc", 2 * faces + cells, [&] { uf::k_drag_bc<T><<<ga, blk, 0, s>>>(sp, uh, vh, wh, cc, u, v, w); });
+    int zc;
+    const dim3 gr = chunk_grid(d.nx, d.ny, d.nz, &zc);
+    L(s, "pressure_rhs", faces + cells, [&] { uf::k_pressure_rhs<T><<<gr, blk, 0, s>>>(sp, u, v, w, b, zc, partials, st); });
+  }
+
+  void rec_post(cudaStream_t s, const T* kin, const T* oin, T* kout, T* oout) {
+    const dim3 blk(uf::BX, uf::BY);
+    const double faces = 3 * N() * tb(), cells = N() * tb();
+    L(s, "project", 2 * faces + cells,
+      [&] { uf::k_project<T><<<plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1), blk, 0, s>>>(sp, p, u, v, w); });
+    L(s, "turbulence", faces + 4 * cells,
+      [&] { uf::k_turbulence<T><<<plane_grid(d.nx, d.ny, d.nz), blk, 0, s>>>(sp, u, v, w, kin, oin, kout, oout); });
+  }
+
+  // One step launched eagerly with per-launch events; aggregates by name.
+  uf_status profile_step(uf_kernel_time* out, int cap_n, int* count, uf_step_stats* stats) override {
+    if (!have_state) return fail(UF_ERR_STATE, "no state: call uf_init_state or uf_set_state first");
+    recs.clear();
+    pool_used = 0;
+    profiling = true;
+    rec_count = 0;
+    const int par = parity;
+    rec_momentum(stream, kb[par], ob[par]);
+    uf_status s = run_solve_eager(stream);
+    if (s == UF_OK) rec_post(stream, kb[par], ob[par], kb[1 - par], ob[1 - par]);
+    profiling = false;
+    if (s != UF_OK) return s;
+    UF_CUDA(cudaStreamSynchronize(stream));
+    UF_CUDA(cudaGetLastError());
+    parity ^= 1;
+    std::vector<uf_kernel_time> agg;
+    for (const Rec& r : recs) {
+      float ms = 0;
+      UF_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+      auto it = std::find_if(agg.begin(), agg.end(), [&](const uf_kernel_time& k) { return r.name == k.name; });
+      if (it == agg.end()) {
+        uf_kernel_time k;
+        std::memset(&k, 0, sizeof(k));
+        std::snprintf(k.name, sizeof(k.name), "%s", r.name.c_str());
+        k.bytes_per_launch = r.bytes;
+        agg.push_back(k);
+        it = agg.end() - 1;
+      }
+      it->launches += 1;
+      it->total_ms += ms;
+    }
+    if (count) *count = (int)agg.size();
+    if (out)
+      for (int i = 0; i < std::min(cap_n, (int)agg.size()); ++i) out[i] = agg[i];
+    last_profile_launches = (int)recs.size();
+    return check_device(stats);
+  }
+  int last_profile_launches = 0;
+
+  // Captures pre(s) ; solve ; post(s) into an executable graph.
+  template <typename Pre, typename Post>
+  uf_status capture(cudaGraphExec_t* exec, Pre pre, Post post, int* n_fixed, int* n_setup, int* n_iter) {
+    cudaGraph_t graph = nullptr;
+    UF_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed));
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cgraph;
+    uf_status rs = UF_OK;
+    cudaError_t e = cudaStreamGetCaptureInfo(cap, &cs, nullptr, &cgraph, nullptr, nullptr, nullptr);
+    cudaGraphConditionalHandle cond;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, cgraph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) {
+      cudaStreamEndCapture(cap, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      return fail(UF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    rec_count = 0;
+    pre(cap);
+    const int fixed_pre = rec_count;
+    rs = rec_solve(cap, cond, n_setup, n_iter);
+    const int after_solve = rec_count;
+    if (rs == UF_OK) post(cap);
+    *n_fixed = fixed_pre + (rec_count - after_solve);
+    e = cudaStreamEndCapture(cap, &graph);
+    if (rs != UF_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rs;
+    }
+    if (e != cudaSuccess) return fail(UF_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(UF_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return UF_OK;
+  }
+
+  uf_status build_step_graphs() {
+    for (int par = 0; par < 2; ++par) {
+      if (step_exec[par]) continue;
+      T* kin = kb[par];
+      T* oin = ob[par];
+      T* kout = kb[1 - par];
+      T* oout = ob[1 - par];
+      int nf, ns, ni;
+      uf_status s = capture(&step_exec[par], [&](cudaStream_t st2) { rec_momentum(st2, kin, oin); },
+                            [&](cudaStream_t st2) { rec_post(st2, kin, oin, kout, oout); }, &nf, &ns, &ni);
+      if (s != UF_OK) return s;
+      launches_fixed = nf;
+      launches_solve_setup = ns;
+      launches_per_iter = ni;
+    }
+    return UF_OK;
+  }
+
+  // ------------------------------------------------------------ entry points
+  uf_status copy_in(T* dst, int lx, int ly, int lz, int pitch, const void* src) {
+    if (!src) return fail(UF_ERR_ARG, "NULL buffer");
+    UF_CUDA(cudaMemcpy2DAsync(dst, (size_t)pitch * sizeof(T), src, (size_t)lx * sizeof(T), (size_t)lx * sizeof(T),
+                              (size_t)ly * lz, cudaMemcpyDefault, stream));
+    return UF_OK;
+  }
+  uf_status copy_out(void* dstp, const T* src, int lx, int ly, int lz, int pitch) {
+    if (!dstp) return fail(UF_ERR_ARG, "NULL buffer");
+    UF_CUDA(cudaMemcpy2DAsync(dstp, (size_t)lx * sizeof(T), src, (size_t)pitch * sizeof(T), (size_t)lx * sizeof(T),
+                              (size_t)ly * lz, cudaMemcpyDefault, stream));
+    UF_CUDA(cudaStreamSynchronize(stream));
+    return UF_OK;
+  }
+
+  uf_status set_porosity(const void* src) override {
+    uf_status s = copy_in(phi, d.nx, d.ny, d.nz, P.Pc, src);
+    if (s != UF_OK) return s;
+    const size_t n = P.n_c;
+    uf::k_drag_coeff<T><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(phi, cc, n, d.Cd, d.a, d.b, d.e);
+    UF_CUDA(cudaGetLastError());
+    return UF_OK;
+  }
+
+  bool field_geom(int f, T** ptr, int* lx, int* ly, int* lz, int* pitch) {
+    *pitch = P.Pc;
+    *lx = d.nx; *ly = d.ny; *lz = d.nz;
+    switch (f) {
+      case UF_FIELD_U: *ptr = u; *lx = d.nx + 1; *pitch = P.Pu; return true;
+      case UF_FIELD_V: *ptr = v; *ly = d.ny + 1; return true;
+      case UF_FIELD_W: *ptr = w; *lz = d.nz + 1; return true;
+      case UF_FIELD_P: *ptr = p; return true;
+      case UF_FIELD_K: *ptr = kb[parity]; return true;
+      case UF_FIELD_OMEGA: *ptr = ob[parity]; return true;
+      case UF_FIELD_PHI: *ptr = phi; return true;
+      case UF_FIELD_NUT: *ptr = nut; return true;
+    }
+    return false;
+  }
+
+  uf_status set_state(int f, const void* src) override {
+    T* ptr; int lx, ly, lz, pitch;
+    if (!field_geom(f, &ptr, &lx, &ly, &lz, &pitch)) return fail(UF_ERR_ARG, "unknown field");
+    if (f == UF_FIELD_PHI) return set_porosity(src);
+    uf_status s = copy_in(ptr, lx, ly, lz, pitch, src);
+    if (s == UF_OK && (f == UF_FIELD_U || f == UF_FIELD_V || f == UF_FIELD_W)) have_state = true;
+    return s;
+  }
+
+  uf_status get_state(int f, void* dst) override {
+    T* ptr; int lx, ly, lz, pitch;
+    if (!field_geom(f, &ptr, &lx, &ly, &lz, &pitch)) return fail(UF_ERR_ARG, "unknown field");
+    return copy_out(dst, ptr, lx, ly, lz, pitch);
+  }
+
+  uf_status init_state() override {
+    if (!init_exec) {
+      int nf, ns, ni;
+      auto pre = [&](cudaStream_t s) {
+        const dim3 blk(uf::BX, uf::BY);
+        const dim3 ga = plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1);
+        uf::k_init_fields<T><<<ga, blk, 0, s>>>(sp, u, v, w, kb[0], ob[0], p);
+        rec_count++;
+        if (!(d.fixed_dt > 0)) {
+          uf::k_cfl_dt<T><<<kDtBlocks, 256, 0, s>>>(u, P.n_u, v, P.n_v, w, P.n_w, d.cfl * d.h, partials, &st->ticket[0], dt);
+          rec_count++;
+        }
+        uf::k_drag_bc<T><<<ga, blk, 0, s>>>(sp, u, v, w, cc, uh, vh, wh);
+        int zc;
+        const dim3 gr = chunk_grid(d.nx, d.ny, d.nz, &zc);
+        uf::k_pressure_rhs<T><<<gr, blk, 0, s>>>(sp, uh, vh, wh, b, zc, partials, st);
+        rec_count += 2;
+      };
+      auto post = [&](cudaStream_t s) {
+        const dim3 blk(uf::BX, uf::BY);
+        uf::k_project<T><<<plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1), blk, 0, s>>>(sp, p, uh, vh, wh);
+        cudaMemcpyAsync(u, uh, P.n_u * sizeof(T), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(v, vh, P.n_v * sizeof(T), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(w, wh, P.n_w * sizeof(T), cudaMemcpyDeviceToDevice, s);
+        rec_count++;
+      };
+      uf_status s = capture(&init_exec, pre, post, &nf, &ns, &ni);
+      if (s != UF_OK) return s;
+    }
+    parity = 0;
+    UF_CUDA(cudaGraphLaunch(init_exec, stream));
+    have_state = true;
+    return check_device(nullptr);
+  }
+
+  // Reads the solver state; returns the device status as a uf_status.
+  uf_status check_device(uf_step_stats* out) {
+    uf::SolveState h;
+    double hdt = 0;
+    UF_CUDA(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, stream));
+    UF_CUDA(cudaMemcpyAsync(&hdt, dt, sizeof(double), cudaMemcpyDeviceToHost, stream));
+    UF_CUDA(cudaStreamSynchronize(stream));
+    last_iters = h.iter;
+    if (out) {
+      out->dt = hdt;
+      out->cg_iters = h.iter;
+      out->cg_rel_residual = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
+      out->status = h.status;
+    }
+    if (h.sticky != 0) {
+      const int code = h.sticky;
+      int zero = 0;
+      UF_CUDA(cudaMemcpyAsync(&st->sticky, &zero, sizeof(int), cudaMemcpyHostToDevice, stream));
+      UF_CUDA(cudaStreamSynchronize(stream));
+      if (code == uf::DEV_NOT_CONVERGED) return fail(UF_ERR_NOT_CONVERGED, "pressure CG reached its iteration cap");
+      if (code == uf::DEV_NAN) return fail(UF_ERR_NAN, "non-finite residual in the pressure solve");
+      return fail(UF_ERR_CUDA, "device reported an error");
+    }
+    return UF_OK;
+  }
+
+  uf_status step(uf_step_stats* out) override {
+    if (!have_state) return fail(UF_ERR_STATE, "no state: call uf_init_state or uf_set_state first");
+    uf_status s = build_step_graphs();
+    if (s != UF_OK) return s;
+    UF_CUDA(cudaGraphLaunch(step_exec[parity], stream));
+    parity ^= 1;
+    if (out) return check_device(out);
+    UF_CUDA(cudaGetLastError());
+    return UF_OK;
+  }
+
+  uf_status run(int nsteps, uf_step_stats* out) override {
+    if (nsteps < 0) return fail(UF_ERR_ARG, "nsteps < 0");
+    for (int n = 0; n < nsteps; ++n) {
+      uf_status s = step(nullptr);
+      if (s != UF_OK) return s;
+    }
+    if (out) return check_device(out);
+    return UF_OK;
+  }
+
+  uf_status objective(double z_lo, double z_hi, double u_hi, double u_lo, double* J) override {
+    if (!J) return fail(UF_ERR_ARG, "NULL output");
+    int k_lo = d.nz, k_hi = -1;
+    for (int k = 0; k < d.nz; ++k) {
+      const double zc = (k + 0.5) * d.h;
+      if (zc >= z_lo && zc <= z_hi) { k_lo = std::min(k_lo, k); k_hi = std::max(k_hi, k); }
+    }
+    if (k_hi < k_lo) { *J = 0.0; return UF_OK; }
+    int zc;
+    const dim3 go = chunk_grid(d.nx, d.ny, k_hi - k_lo + 1, &zc);
+    uf::k_objective<T><<<go, dim3(uf::BX, uf::BY), 0, stream>>>(sp, u, v, w, k_lo, k_hi, zc, u_hi, u_lo, partials,
+                                                                 &st->ticket[0], scal);
+    UF_CUDA(cudaGetLastError());
+    UF_CUDA(cudaMemcpyAsync(J, scal, sizeof(double), cudaMemcpyDeviceToHost, stream));
+    UF_CUDA(cudaStreamSynchronize(stream));
+    return UF_OK;
+  }
+
+  uf_status divergence(double* outv) override {
+    if (!outv) return fail(UF_ERR_ARG, "NULL output");
+    int zc;
+    const dim3 gd = chunk_grid(d.nx, d.ny, d.nz, &zc);
+    uf::k_divergence<T><<<gd, dim3(uf::BX, uf::BY), 0, stream>>>(sp, u, v, w, zc, partials, &st->ticket[0], scal + 2);
+    UF_CUDA(cudaGetLastError());
+    double h2[2];
+    UF_CUDA(cudaMemcpyAsync(h2, scal + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    UF_CUDA(cudaStreamSynchronize(stream));
+    *outv = h2[1] > 0 ? std::sqrt(h2[0] / h2[1]) : std::sqrt(h2[0]);
+    return UF_OK;
+  }
+
+  uf_status apply_poisson(const void* x, void* y) override {
+    uf_status s = copy_in(q, d.nx, d.ny, d.nz, P.Pc, x);
+    if (s != UF_OK) return s;
+    int zc;
+    dim3 g = chunk_grid(d.nx, d.ny, d.nz, &zc);
+    uf::k_apply_level<T><<<g, dim3(uf::BX, uf::BY), 0, stream>>>(lv[0], q, d0, zc);
+    UF_CUDA(cudaGetLastError());
+    return copy_out(y, d0, d.nx, d.ny, d.nz, P.Pc);
+  }
+
+  uf_status poisson_solve(const void* bsrc, int* iters, double* rel) override {
+    uf_status s = copy_in(b, d.nx, d.ny, d.nz, P.Pc, bsrc);
+    if (s != UF_OK) return s;
+    if (!solve_exec) {
+      int nf, ns, ni;
+      auto pre = [&](cudaStream_t s2) {
+        int zc;
+        dim3 g = chunk_grid(d.nx, d.ny, d.nz, &zc);
+        uf::k_solve_reset<T><<<g, dim3(uf::BX, uf::BY), 0, s2>>>(lv[0], b, zc, partials, st);
+        rec_count++;
+      };
+      auto post = [&](cudaStream_t) {};
+      s = capture(&solve_exec, pre, post, &nf, &ns, &ni);
+      if (s != UF_OK) return s;
+    }
+    UF_CUDA(cudaGraphLaunch(solve_exec, stream));
+    uf_step_stats o;
+    s = check_device(&o);
+    if (iters) *iters = o.cg_iters;
+    if (rel) *rel = o.cg_rel_residual;
+    return s;
+  }
+
+  int last_launches() override {
+    if (last_iters < 0) return 0;
+    return launches_fixed + launches_solve_setup + last_iters * launches_per_iter;
+  }
+};
+
+}  // namespace
+
+// ============================================================== C ABI ====
+
+extern "C" {
+
+void uf_default_desc(uf_grid_desc* d) {
+  if (!d) return;
+  std::memset(d, 0, sizeof(*d));
+  d->nx = 64; d->ny = 32; d->nz = 16; d->h = 2.0;
+  d->precision = UF_F32;
+  d->wind_dir_deg = 0.0; d->u_ref = 5.0; d->z_ref = 10.0; d->z0 = 0.5;
+  d->inflow_loglaw = 0; d->ground_noslip = 1;
+  d->rho = 1.225; d->nu = 1.5e-5; d->Cd = 1.0; d->a = 0.62; d->b = 2.5; d->e = 1e-10;
+  d->I = 0.1; d->L = 10.0;
+  d->C_mu = 0.09; d->alpha = 0.52; d->beta = 0.0708; d->sigma = 0.5; d->sigma_star = 0.6; d->C_lim = 7.0 / 8.0;
+  d->cfl = 0.5; d->fixed_dt = 0.0; d->k_min = 1e-10; d->omega_min = 1e-6;
+  d->precond = UF_PRECOND_MG; d->cg_tol = 0.0; d->cg_max_iter = 200;
+  d->ai_omega = 1.65; d->mg_jacobi_omega = 6.0 / 7.0; d->mg_coarse_max = 512;
+  d->mg_smoother = UF_SMOOTH_JACOBI;
+}
+
+size_t uf_workspace_bytes(const uf_grid_desc* d) {
+  std::string why;
+  if (!desc_valid(d, &why)) {
+    g_err = why;
+    return 0;
+  }
+  return make_plan(d).total;
+}
+
+uf_status uf_create_grid(const uf_grid_desc* d, void* d_workspace, size_t bytes, void* stream, uf_grid** out) {
+  std::string why;
+  if (!out) return fail(UF_ERR_ARG, "NULL output handle");
+  *out = nullptr;
+  if (!desc_valid(d, &why)) return fail(UF_ERR_ARG, why);
+  if (!d_workspace) return fail(UF_ERR_ARG, "NULL workspace");
+  if (!stream) return fail(UF_ERR_ARG, "pass a created CUDA stream (the legacy default stream cannot be captured)");
+  const Plan P = make_plan(d);
+  if (bytes < P.total) return fail(UF_ERR_NOMEM, "workspace smaller than uf_workspace_bytes()");
+  uf_grid* g = nullptr;
+  uf_status s;
+  if (d->precision == UF_F64) {
+    auto* gi = new GridImpl<double>();
+    s = gi->setup(d, d_workspace, (cudaStream_t)stream);
+    g = gi;
+  } else {
+    auto* gi = new GridImpl<float>();
+    s = gi->setup(d, d_workspace, (cudaStream_t)stream);
+    g = gi;
+  }
+  if (s != UF_OK) {
+    delete g;
+    return s;
+  }
+  *out = g;
+  return UF_OK;
+}
+
+uf_status uf_destroy(uf_grid* g) {
+  if (!g) return fail(UF_ERR_ARG, "NULL grid");
+  delete g;
+  return UF_OK;
+}
+
+#define UF_NEED(g) if (!(g)) return fail(UF_ERR_ARG, "NULL grid")
+
+uf_status uf_set_porosity(uf_grid* g, const void* phi) { UF_NEED(g); return g->set_porosity(phi); }
+uf_status uf_set_state(uf_grid* g, int f, const void* b) { UF_NEED(g); return g->set_state(f, b); }
+uf_status uf_get_state(uf_grid* g, int f, void* b) { UF_NEED(g); return g->get_state(f, b); }
+uf_status uf_init_state(uf_grid* g) { UF_NEED(g); return g->init_state(); }
+uf_status uf_step(uf_grid* g, uf_step_stats* s) { UF_NEED(g); return g->step(s); }
+uf_status uf_run(uf_grid* g, int n, uf_step_stats* s) { UF_NEED(g); return g->run(n, s); }
+uf_status uf_objective(uf_grid* g, double z_lo, double z_hi, double u_hi, double u_lo, double* J) {
+  UF_NEED(g);
+  return g->objective(z_lo, z_hi, u_hi, u_lo, J);
+}
+uf_status uf_divergence(uf_grid* g, double* out) { UF_NEED(g); return g->divergence(out); }
+uf_status uf_apply_poisson(uf_grid* g, const void* x, void* y) { UF_NEED(g); return g->apply_poisson(x, y); }
+uf_status uf_poisson_solve(uf_grid* g, const void* b, int* iters, double* rel) {
+  UF_NEED(g);
+  return g->poisson_solve(b, iters, rel);
+}
+int uf_last_step_launches(uf_grid* g) { return g ? g->last_launches() : 0; }
+uf_status uf_profile_step(uf_grid* g, uf_kernel_time* out, int capacity, int* count, uf_step_stats* stats) {
+  UF_NEED(g);
+  if (capacity < 0) return fail(UF_ERR_ARG, "negative capacity");
+  return g->profile_step(out, capacity, count, stats);
+}
+const char* uf_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

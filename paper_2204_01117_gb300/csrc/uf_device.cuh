@@ -1,0 +1,167 @@
+// Device-side building blocks of the UrbanFlow RANS step (sm_103a).
+//
+// Grid: uniform staggered MAC grid (Sec. 3, "Discretization and Numerical
+// Integration"): u on x-faces, v on y-faces, w on z-faces, p / k / omega /
+// porosity at cell centres.  Every lattice is stored x-fastest with its row
+// pitch rounded up to 32 elements so that rows start on 128-byte
+// boundaries; padding is zero and never written.
+//
+// Boundary conditions (Sec. 3, "Porosity Model vs. Solid-wall Boundary
+// Conditions") are evaluated on the fly by the consumers of a field instead of
+// being materialised by separate passes:
+//   * normal component on a boundary face: inlet -> inflow profile, outlet ->
+//     value of the adjacent interior face (zero normal derivative), slip or
+//     no-slip wall -> 0;
+//   * tangential ghost beyond a side: inlet -> inflow value, outlet / slip ->
+//     mirror of the interior value, no-slip -> its negative.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace uf {
+
+enum SideType { INFLOW = 0, OUTFLOW = 1, SLIP = 2, NOSLIP = 3 };
+
+// Solver state word written by kernels (first error wins).
+enum DevStatus { DEV_OK = 0, DEV_NOT_CONVERGED = 4, DEV_NAN = 5 };
+
+template <typename T>
+struct StepParams {
+  int nx, ny, nz;
+  int Pu;     // row pitch of the u lattice (nx+1 rounded up)
+  int Pc;     // row pitch of the v, w and cell lattices (nx rounded up)
+  int side[6];   // x-, x+, y-, y+, z-, z+
+  T h, inv_h;
+  T dirx, diry;            // horizontal wind direction (cos, sin)
+  T rho, nu;
+  T C_mu, alpha, beta, sigma, sigma_star, C_lim;
+  T k_min, om_min, k_in, om_in;
+  const T* prof;           // inflow speed at the nz cell-centre heights
+  const double* dt;        // device scalar: the step's time step
+};
+
+// ------------------------------------------------------------- indexing --
+template <typename T>
+__device__ __forceinline__ size_t idx_u(const StepParams<T>& p, int i, int j, int k) {
+  return (size_t)i + (size_t)p.Pu * ((size_t)j + (size_t)p.ny * k);
+}
+template <typename T>
+__device__ __forceinline__ size_t idx_v(const StepParams<T>& p, int i, int j, int k) {
+  return (size_t)i + (size_t)p.Pc * ((size_t)j + (size_t)(p.ny + 1) * k);
+}
+template <typename T>   // w lattice and cell lattice share the x-y layout
+__device__ __forceinline__ size_t idx_c(const StepParams<T>& p, int i, int j, int k) {
+  return (size_t)i + (size_t)p.Pc * ((size_t)j + (size_t)p.ny * k);
+}
+
+// ------------------------------------------------------ boundary values --
+template <typename T>
+__device__ __forceinline__ T normal_face(int side, T adjacent, T inflow) {
+  return side == INFLOW ? inflow : (side == OUTFLOW ? adjacent : T(0));
+}
+template <typename T>
+__device__ __forceinline__ T tangential_ghost(int side, T q, T inflow) {
+  return side == INFLOW ? inflow : (side == NOSLIP ? -q : q);
+}
+
+// Face values with the BC applied on boundary faces (the stored value there
+// is never read).
+template <typename T>
+__device__ __forceinline__ T u_face(const T* __restrict__ u, const StepParams<T>& p, int i, int j, int k) {
+  if (i == 0) return normal_face(p.side[0], u[idx_u(p, 1, j, k)], p.prof[k] * p.dirx);
+  if (i == p.nx) return normal_face(p.side[1], u[idx_u(p, p.nx - 1, j, k)], p.prof[k] * p.dirx);
+  return u[idx_u(p, i, j, k)];
+}
+template <typename T>
+__device__ __forceinline__ T v_face(const T* __restrict__ v, const StepParams<T>& p, int i, int j, int k) {
+  if (j == 0) return normal_face(p.side[2], v[idx_v(p, i, 1, k)], p.prof[k] * p.diry);
+  if (j == p.ny) return normal_face(p.side[3], v[idx_v(p, i, p.ny - 1, k)], p.prof[k] * p.diry);
+  return v[idx_v(p, i, j, k)];
+}
+template <typename T>
+__device__ __forceinline__ T w_face(const T* __restrict__ w, const StepParams<T>& p, int i, int j, int k) {
+  if (k == 0 || k == p.nz) return T(0);
+  return w[idx_c(p, i, j, k)];
+}
+
+// ------------------------------------------------------------- reduction --
+// Deterministic block + grid reduction in FP64: every block writes one
+// partial; the last block to finish (atomic ticket) sums the partials in a
+// fixed order and runs `finish(total)` on thread 0.  The ticket is reset by
+// the last block, so the kernel can be replayed.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = (threadIdx.x + blockDim.x * threadIdx.y) >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = (lane < NT / 32) ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;   // valid on thread 0 of the block
+}
+
+template <int NT>
+__device__ __forceinline__ double block_max(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, warp = (threadIdx.x + blockDim.x * threadIdx.y) >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = (lane < NT / 32) ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+  }
+  return t;
+}
+
+__device__ __forceinline__ int block_linear_id() {
+  return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+}
+__device__ __forceinline__ int grid_blocks() { return gridDim.x * gridDim.y * gridDim.z; }
+__device__ __forceinline__ int thread_linear_id() { return threadIdx.x + blockDim.x * threadIdx.y; }
+
+// Publishes this block's partial(s) and returns true in the last block.
+template <int NV>
+__device__ __forceinline__ bool publish_partials(double* partials, unsigned int* ticket, const double* vals,
+                                                 bool* sh_last) {
+  if (thread_linear_id() == 0) {
+    const int b = block_linear_id(), nb = grid_blocks();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) partials[q * nb + b] = vals[q];
+    __threadfence();
+    const unsigned int t = atomicAdd(ticket, 1u);
+    *sh_last = (t == (unsigned)nb - 1);
+  }
+  __syncthreads();
+  return *sh_last;
+}
+
+// In the last block: sum partials[q*nb ..] for q < NV in a fixed order.
+template <int NT, int NV>
+__device__ __forceinline__ void reduce_partials_sum(const double* partials, double* out, double* sh) {
+  const int nb = grid_blocks();
+  for (int q = 0; q < NV; ++q) {
+    double s = 0.0;
+    for (int b = thread_linear_id(); b < nb; b += NT) s += __ldcg(partials + q * nb + b);
+    s = block_sum<NT>(s, sh);
+    if (thread_linear_id() == 0) out[q] = s;
+  }
+}
+template <int NT>
+__device__ __forceinline__ double reduce_partials_max(const double* partials, double* sh) {
+  const int nb = grid_blocks();
+  double s = 0.0;
+  for (int b = thread_linear_id(); b < nb; b += NT) s = fmax(s, __ldcg(partials + b));
+  return block_max<NT>(s, sh);
+}
+
+}  // namespace uf

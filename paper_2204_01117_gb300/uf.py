@@ -1,0 +1,302 @@
+"""ctypes binding of the C ABI in ``include/uf.h`` (argument marshalling only).
+
+Every step of the solver runs in the CUDA library ``_build/libuf.so``; this
+module builds nothing at import time and has no fallback: if the library is
+missing, ``load()`` raises.  PyTorch supplies device memory (the workspace) and
+the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(_HERE)
+CSRC = os.path.join(_HERE, "csrc")
+LIB_PATH = os.path.join(_HERE, "_build", "libuf.so")
+HEADER = os.path.join(ROOT, "include", "uf.h")
+SOURCES = ["capi.cu"]
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo",
+              "--expt-extended-lambda", "-Xcompiler", "-fPIC", "-shared"]
+
+UF_OK, UF_ERR_ARG, UF_ERR_CUDA, UF_ERR_NOMEM, UF_ERR_NOT_CONVERGED, UF_ERR_NAN, UF_ERR_TIMEOUT, UF_ERR_STATE = range(8)
+STATUS_NAMES = ["UF_OK", "UF_ERR_ARG", "UF_ERR_CUDA", "UF_ERR_NOMEM", "UF_ERR_NOT_CONVERGED", "UF_ERR_NAN",
+                "UF_ERR_TIMEOUT", "UF_ERR_STATE"]
+F32, F64 = 0, 1
+PRECOND = {"mg": 0, "ai1": 1, "jacobi": 2, "none": 3}
+SMOOTHER = {"jacobi": 0, "rbgs": 1}
+FIELDS = {"u": 0, "v": 1, "w": 2, "p": 3, "k": 4, "omega": 5, "phi": 6, "nut": 7}
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("h", ctypes.c_double), ("precision", ctypes.c_int),
+        ("wind_dir_deg", ctypes.c_double), ("u_ref", ctypes.c_double),
+        ("z_ref", ctypes.c_double), ("z0", ctypes.c_double),
+        ("inflow_loglaw", ctypes.c_int), ("ground_noslip", ctypes.c_int),
+        ("rho", ctypes.c_double), ("nu", ctypes.c_double), ("Cd", ctypes.c_double),
+        ("a", ctypes.c_double), ("b", ctypes.c_double), ("e", ctypes.c_double),
+        ("I", ctypes.c_double), ("L", ctypes.c_double),
+        ("C_mu", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+        ("sigma", ctypes.c_double), ("sigma_star", ctypes.c_double), ("C_lim", ctypes.c_double),
+        ("cfl", ctypes.c_double), ("fixed_dt", ctypes.c_double),
+        ("k_min", ctypes.c_double), ("omega_min", ctypes.c_double),
+        ("precond", ctypes.c_int), ("cg_tol", ctypes.c_double), ("cg_max_iter", ctypes.c_int),
+        ("ai_omega", ctypes.c_double), ("mg_jacobi_omega", ctypes.c_double),
+        ("mg_coarse_max", ctypes.c_int), ("mg_smoother", ctypes.c_int),
+    ]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("cg_iters", ctypes.c_int),
+                ("cg_rel_residual", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int), ("total_ms", ctypes.c_double),
+                ("bytes_per_launch", ctypes.c_double)]
+
+
+class UFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the CUDA sources into _build/libuf.so for sm_103a (nvcc)."""
+    with _lock:
+        srcs = [os.path.join(CSRC, s) for s in SOURCES]
+        deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")] + [HEADER]
+        if (not force and os.path.exists(LIB_PATH)
+                and os.path.getmtime(LIB_PATH) >= max(os.path.getmtime(p) for p in deps)):
+            return LIB_PATH
+        os.makedirs(os.path.dirname(LIB_PATH), exist_ok=True)
+        tmp = LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["nvcc", *NVCC_FLAGS, *srcs, "-o", tmp]
+        if verbose:
+            print(" ".join(cmd))
+        subprocess.check_call(cmd)
+        os.replace(tmp, LIB_PATH)
+        return LIB_PATH
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/uf.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(uf_[a-z_0-9]+)\s*\(", text)))
+
+
+def load():
+    """Load _build/libuf.so; raises OSError when it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise OSError(f"{LIB_PATH} is missing: run paper_2204_01117_gb300.uf.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    P = ctypes.POINTER
+    lib.uf_default_desc.argtypes = [P(GridDesc)]
+    lib.uf_default_desc.restype = None
+    lib.uf_workspace_bytes.argtypes = [P(GridDesc)]
+    lib.uf_workspace_bytes.restype = ctypes.c_size_t
+    lib.uf_create_grid.argtypes = [P(GridDesc), vp, ctypes.c_size_t, vp, P(vp)]
+    lib.uf_destroy.argtypes = [vp]
+    lib.uf_set_porosity.argtypes = [vp, vp]
+    lib.uf_set_state.argtypes = [vp, ip, vp]
+    lib.uf_get_state.argtypes = [vp, ip, vp]
+    lib.uf_init_state.argtypes = [vp]
+    lib.uf_step.argtypes = [vp, P(StepStats)]
+    lib.uf_run.argtypes = [vp, ip, P(StepStats)]
+    lib.uf_objective.argtypes = [vp, dp, dp, dp, dp, P(dp)]
+    lib.uf_divergence.argtypes = [vp, P(dp)]
+    lib.uf_apply_poisson.argtypes = [vp, vp, vp]
+    lib.uf_poisson_solve.argtypes = [vp, vp, P(ip), P(dp)]
+    lib.uf_last_step_launches.argtypes = [vp]
+    lib.uf_last_step_launches.restype = ip
+    lib.uf_last_error.restype = ctypes.c_char_p
+    lib.uf_profile_step.argtypes = [vp, P(KernelTime), ip, P(ip), P(StepStats)]
+    lib.uf_profile_step.restype = ip
+    for name in ("uf_create_grid", "uf_destroy", "uf_set_porosity", "uf_set_state", "uf_get_state",
+                 "uf_init_state", "uf_step", "uf_run", "uf_objective", "uf_divergence",
+                 "uf_apply_poisson", "uf_poisson_solve"):
+        getattr(lib, name).restype = ip
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().uf_last_error().decode()
+
+
+def check(status: int) -> None:
+    if status != UF_OK:
+        raise UFError(status, last_error())
+
+
+def default_desc(**overrides) -> GridDesc:
+    d = GridDesc()
+    load().uf_default_desc(ctypes.byref(d))
+    for k, v in overrides.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"f32": F32, "f64": F64}[v]
+        if k == "precond" and isinstance(v, str):
+            v = PRECOND[v]
+        if k == "mg_smoother" and isinstance(v, str):
+            v = SMOOTHER[v]
+        if not hasattr(d, k):
+            raise TypeError(f"unknown grid parameter {k!r}")
+        setattr(d, k, v)
+    return d
+
+
+def workspace_bytes(desc: GridDesc) -> int:
+    return int(load().uf_workspace_bytes(ctypes.byref(desc)))
+
+
+def _ptr(buf, dtype):
+    """(pointer, keep-alive) of a torch tensor (device or host) or numpy array."""
+    try:
+        import torch
+        if isinstance(buf, torch.Tensor):
+            if buf.dtype != dtype[0] or not buf.is_contiguous():
+                raise TypeError(f"expected a contiguous {dtype[0]} tensor")
+            return ctypes.c_void_p(buf.data_ptr()), buf
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(buf, dtype=dtype[1])
+    return ctypes.c_void_p(arr.ctypes.data), arr
+
+
+class Grid:
+    """One simulation grid on the current CUDA device (see include/uf.h)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, precision: str = "f32", stream=None, **params):
+        import torch
+        self.lib = load()
+        self.desc = default_desc(nx=nx, ny=ny, nz=nz, precision=precision, **params)
+        if precision == "f64":
+            self.torch_dtype, self.np_dtype = torch.float64, np.float64
+        else:
+            self.torch_dtype, self.np_dtype = torch.float32, np.float32
+        nbytes = workspace_bytes(self.desc)
+        if nbytes == 0:
+            raise UFError(UF_ERR_ARG, last_error())
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        h = ctypes.c_void_p()
+        check(self.lib.uf_create_grid(ctypes.byref(self.desc), ctypes.c_void_p(self.workspace.data_ptr()),
+                                      nbytes, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self._h = h
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.shapes = {"u": (nz, ny, nx + 1), "v": (nz, ny + 1, nx), "w": (nz + 1, ny, nx),
+                       "p": (nz, ny, nx), "k": (nz, ny, nx), "omega": (nz, ny, nx),
+                       "phi": (nz, ny, nx), "nut": (nz, ny, nx)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.uf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def dtypes(self):
+        return (self.torch_dtype, self.np_dtype)
+
+    def set_porosity(self, phi) -> None:
+        ptr, keep = _ptr(phi, self.dtypes)
+        check(self.lib.uf_set_porosity(self._h, ptr))
+
+    def set_state(self, name: str, value) -> None:
+        if np.isscalar(value):
+            value = np.full(self.shapes[name], value, dtype=self.np_dtype)
+        ptr, keep = _ptr(value, self.dtypes)
+        check(self.lib.uf_set_state(self._h, FIELDS[name], ptr))
+
+    def get_state(self, name: str, out=None):
+        """Returns the field as a numpy array (host), or fills ``out``."""
+        if out is None:
+            out = np.empty(self.shapes[name], dtype=self.np_dtype)
+        ptr, keep = _ptr(out, self.dtypes)
+        check(self.lib.uf_get_state(self._h, FIELDS[name], ptr))
+        return out
+
+    def init_state(self) -> None:
+        check(self.lib.uf_init_state(self._h))
+
+    def step(self, stats: bool = True):
+        if not stats:
+            check(self.lib.uf_step(self._h, None))
+            return None
+        s = StepStats()
+        check(self.lib.uf_step(self._h, ctypes.byref(s)))
+        return s
+
+    def run(self, nsteps: int, stats: bool = True):
+        s = StepStats()
+        check(self.lib.uf_run(self._h, nsteps, ctypes.byref(s) if stats else None))
+        return s if stats else None
+
+    def objective(self, z_lo=1.0, z_hi=3.0, u_hi=4.0, u_lo=1.0) -> float:
+        J = ctypes.c_double()
+        check(self.lib.uf_objective(self._h, z_lo, z_hi, u_hi, u_lo, ctypes.byref(J)))
+        return J.value
+
+    def divergence(self) -> float:
+        out = ctypes.c_double()
+        check(self.lib.uf_divergence(self._h, ctypes.byref(out)))
+        return out.value
+
+    def apply_poisson(self, x):
+        xin, keep = _ptr(x, self.dtypes)
+        y = np.empty(self.shapes["p"], dtype=self.np_dtype)
+        yp, keep2 = _ptr(y, self.dtypes)
+        check(self.lib.uf_apply_poisson(self._h, xin, yp))
+        return y
+
+    def poisson_solve(self, b):
+        bp, keep = _ptr(b, self.dtypes)
+        it, rel = ctypes.c_int(), ctypes.c_double()
+        check(self.lib.uf_poisson_solve(self._h, bp, ctypes.byref(it), ctypes.byref(rel)))
+        return it.value, rel.value
+
+    def profile_step(self):
+        """One eagerly launched, event-timed step; returns (stats, {label: dict})."""
+        cap = 128
+        arr = (KernelTime * cap)()
+        n = ctypes.c_int()
+        s = StepStats()
+        check(self.lib.uf_profile_step(self._h, arr, cap, ctypes.byref(n), ctypes.byref(s)))
+        out = {}
+        for i in range(min(n.value, cap)):
+            k = arr[i]
+            out[k.name.decode()] = dict(launches=k.launches, total_ms=k.total_ms,
+                                        bytes_per_launch=k.bytes_per_launch)
+        return s, out
+
+    def launches_last_step(self) -> int:
+        return int(self.lib.uf_last_step_launches(self._h))
+
+    def state(self) -> dict:
+        return {n: self.get_state(n) for n in ("u", "v", "w", "p", "k", "omega")}
+
+    def set_fields(self, st: dict) -> None:
+        for n, val in st.items():
+            self.set_state(n, np.asarray(val, dtype=self.np_dtype))

@@ -1,0 +1,61 @@
+"""C-ABI library: builds, loads without a GPU, exports every declared symbol,
+and validates descriptions on the host."""
+import ctypes
+
+import pytest
+
+from paper_2204_01117_gb300 import uf
+
+
+@pytest.fixture(scope="module")
+def lib():
+    uf.build()
+    return uf.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = uf.declared_functions()
+    assert len(names) >= 16
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    for n in ("uf_create_grid", "uf_set_porosity", "uf_step", "uf_run", "uf_objective"):
+        assert n in names
+
+
+def test_default_desc_paper_constants(lib):
+    d = uf.default_desc()
+    assert (d.C_mu, d.alpha, d.beta, d.sigma, d.sigma_star) == (0.09, 0.52, 0.0708, 0.5, 0.6)
+    assert d.C_lim == 7.0 / 8.0
+    assert (d.a, d.b, d.e, d.Cd) == (0.62, 2.5, 1e-10, 1.0)
+    assert d.precond == uf.PRECOND["mg"] and d.cg_tol == 0.0 and d.cg_max_iter == 200
+    assert d.mg_smoother == uf.SMOOTHER["jacobi"]
+    assert d.ai_omega == 1.65 and d.cfl == 0.5
+
+
+@pytest.mark.parametrize("bad,msg", [
+    (dict(nx=1), "nx"), (dict(h=0.0), "h must"), (dict(precision=7), "precision"),
+    (dict(u_ref=0.0), "u_ref"), (dict(precond=9), "preconditioner"), (dict(cg_tol=-1.0), "cg_tol"), (dict(mg_smoother=5), "smoother"),
+    (dict(ai_omega=2.0), "ai_omega"), (dict(inflow_loglaw=1, z0=0.0), "log law"),
+])
+def test_invalid_descriptions_rejected_on_host(lib, bad, msg):
+    d = uf.default_desc(**bad)
+    assert uf.workspace_bytes(d) == 0
+    assert msg in uf.last_error()
+
+
+def test_workspace_size_scales(lib):
+    small = uf.workspace_bytes(uf.default_desc(nx=64, ny=32, nz=16))
+    big = uf.workspace_bytes(uf.default_desc(nx=256, ny=256, nz=64))
+    f64 = uf.workspace_bytes(uf.default_desc(nx=256, ny=256, nz=64, precision="f64"))
+    assert 0 < small < big < f64
+    # ~25 cell-sized FP32 arrays plus multigrid levels for the 4.2M-cell grid
+    assert 80 * 4194304 < big < 140 * 4194304
+
+
+def test_null_arguments_are_errors(lib):
+    h = ctypes.c_void_p()
+    d = uf.default_desc()
+    assert lib.uf_create_grid(ctypes.byref(d), None, 0, None, ctypes.byref(h)) == uf.UF_ERR_ARG
+    assert lib.uf_step(None, None) == uf.UF_ERR_ARG
+    assert lib.uf_destroy(None) == uf.UF_ERR_ARG
+    assert lib.uf_last_step_launches(None) == 0

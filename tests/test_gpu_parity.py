@@ -1,0 +1,271 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: FP64 grids agree with the oracle to the pressure-solver
+tolerances (GPU CG 1e-12, oracle 1e-13); FP32 grids stay within 1e-5 relative
+L2 per field and step, and within 1e-3 after a long run.  Sizes span several
+32 x 8 thread tiles with ragged tails (e.g. 45 x 37).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_01117_gb300 import layouts, uf
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FIELDS6 = ("u", "v", "w", "p", "k", "omega")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    uf.build()
+    uf.load()
+    oracle.build()
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def pair(sc, precision="f32", **gp):
+    o = oracle.Oracle(sc.nx, sc.ny, sc.nz, **sc.params())
+    o.set("phi", sc.phi)
+    g = uf.Grid(sc.nx, sc.ny, sc.nz, precision=precision, **sc.params(), **gp)
+    g.set_porosity(sc.phi.astype(g.np_dtype))
+    return o, g
+
+
+def ragged_urban(nx=45, ny=37, nz=11, seed=2, deg=0.0, h=2.0):
+    return layouts.urban_block(nx, ny, nz, h=h, n_boxes=3, n_trees=4, seed=seed, footprint=(6.0, 14.0),
+                               height=(4.0, 14.0), radius=(2.0, 4.0), wind_dir_deg=deg, margin=0.1)
+
+
+# ------------------------------------------------------------ Poisson ---
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+@pytest.mark.parametrize("dims,deg", [((45, 37, 11), 135.0), ((70, 33, 9), 0.0), ((33, 64, 1), 90.0)])
+def test_poisson_operator(precision, dims, deg):
+    nx, ny, nz = dims
+    o = oracle.Oracle(nx, ny, nz, wind_dir_deg=deg)
+    g = uf.Grid(nx, ny, nz, precision=precision, wind_dir_deg=deg)
+    x = np.random.default_rng(0).standard_normal((nz, ny, nx))
+    y = g.apply_poisson(x.astype(g.np_dtype))
+    ref = o.apply_A(x.astype(g.np_dtype).astype(np.float64))
+    tol = 1e-14 if precision == "f64" else 2e-7
+    assert rel(y, ref) <= tol
+
+
+@pytest.mark.parametrize("precond", ["mg", "mg-rbgs", "ai1", "jacobi", "none"])
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_poisson_solve(precond, precision):
+    nx, ny, nz = 45, 37, 11
+    tol = 1e-12 if precision == "f64" else 1e-7
+    o = oracle.Oracle(nx, ny, nz, wind_dir_deg=30.0)
+    extra = {"mg_smoother": "rbgs"} if precond == "mg-rbgs" else {}
+    g = uf.Grid(nx, ny, nz, precision=precision, wind_dir_deg=30.0, precond=precond.split("-")[0], cg_tol=tol,
+                cg_max_iter=5000, **extra)
+    b = np.random.default_rng(1).standard_normal((nz, ny, nx))
+    ref, _, _ = o.cg(b, tol=1e-13)
+    g.set_state("p", 0.0)
+    it, r = g.poisson_solve(b.astype(g.np_dtype))
+    assert r <= tol
+    x = g.get_state("p")
+    assert rel(x, ref) <= (1e-9 if precision == "f64" else 5e-5), (precond, it)
+
+
+def test_preconditioner_iteration_ordering():
+    nx, ny, nz = 64, 48, 16
+    b = np.random.default_rng(5).standard_normal((nz, ny, nx))
+    its = {}
+    for pc in ("mg", "ai1", "jacobi", "none"):
+        g = uf.Grid(nx, ny, nz, precision="f64", precond=pc, cg_tol=1e-10, cg_max_iter=5000)
+        g.set_state("p", 0.0)
+        its[pc], _ = g.poisson_solve(b)
+    assert its["mg"] < its["ai1"] < its["none"], its
+    # Tables 2-3: Jacobi barely changes the condition number of this operator
+    assert abs(its["jacobi"] - its["none"]) <= 0.05 * its["none"], its
+    # App. A.3: the AI relaxation is best around w = 1.6-1.7; w = 1 is worse
+    g1 = uf.Grid(nx, ny, nz, precision="f64", precond="ai1", ai_omega=1.0, cg_tol=1e-10, cg_max_iter=5000)
+    g1.set_state("p", 0.0)
+    it1, _ = g1.poisson_solve(b)
+    assert its["ai1"] <= it1, (its["ai1"], it1)
+
+
+# -------------------------------------------------------------- steps ---
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_init_state(precision):
+    sc = ragged_urban()
+    o, g = pair(sc, precision)
+    o.init()
+    g.init_state()
+    tol = 1e-10 if precision == "f64" else 1e-5
+    for n in FIELDS6:
+        assert rel(g.get_state(n), o.get(n)) <= tol, n
+
+
+@pytest.mark.parametrize("deg", [0.0, 135.0, 300.0])
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_one_step_from_shared_state(precision, deg):
+    sc = ragged_urban(deg=deg)
+    o, g = pair(sc, precision, mg_smoother="rbgs" if deg == 135.0 else "jacobi")
+    o.init()
+    for _ in range(3):
+        o.step()
+    g.set_fields(o.state())
+    st = g.step()
+    ost = o.step()
+    assert st.dt == pytest.approx(ost.dt, rel=1e-6)
+    tol = 1e-10 if precision == "f64" else 1e-5
+    for n in FIELDS6:
+        assert rel(g.get_state(n), o.get(n)) <= tol, (n, rel(g.get_state(n), o.get(n)))
+    assert g.divergence() <= (1e-10 if precision == "f64" else 1e-6)
+
+
+def test_single_box_fp64_100_steps_every_step():
+    sc = layouts.single_box()          # 64 x 32 x 16, h = 2 m, one solid box
+    o, g = pair(sc, "f64", cg_tol=1e-12)
+    o.init()
+    g.init_state()
+    worst = 0.0
+    for n in range(100):
+        st = g.step()
+        o.step()
+        assert st.status == 0
+        for f in FIELDS6:
+            e = rel(g.get_state(f), o.get(f))
+            worst = max(worst, e)
+            assert e <= 1e-8, (n, f, e)
+    assert g.divergence() <= 1e-10
+
+
+def test_fp32_long_run_within_1e3():
+    sc = layouts.urban_block(48, 40, 16, h=2.0, n_boxes=4, n_trees=6, seed=7, footprint=(6.0, 16.0),
+                             height=(6.0, 20.0), radius=(2.0, 5.0), u_ref=3.0)
+    o, g = pair(sc, "f32")
+    o.init()
+    g.init_state()
+    for n in range(300):
+        g.step(stats=False)
+        o.step()
+    st = g.step()
+    o.step()
+    assert st.status == 0
+    for f in FIELDS6:
+        e = rel(g.get_state(f), o.get(f))
+        assert e <= 1e-3, (f, e)
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_uniform_flow_bitwise(precision):
+    sc = layouts.empty_domain(40, 20, 9, h=1.0, u_ref=2.0, ground_noslip=False)
+    g = uf.Grid(sc.nx, sc.ny, sc.nz, precision=precision, **sc.params())
+    g.init_state()
+    for _ in range(10):
+        st = g.step()
+        assert st.dt == 0.25
+    assert np.all(g.get_state("u") == 2.0)
+    assert np.all(g.get_state("v") == 0.0) and np.all(g.get_state("w") == 0.0)
+    assert np.all(g.get_state("p") == 0.0)
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_porous_slab_pressure_drop(precision):
+    nx, ny, nz, h, U = 40, 8, 4, 1.0, 2.0
+    phi = np.ones((nz, ny, nx))
+    phi[:, :, 15:25] = 0.5
+    sc = layouts.Scenario(nx, ny, nz, h, phi, u_ref=U, ground_noslip=False)
+    g = uf.Grid(nx, ny, nz, precision=precision, **sc.params(),
+                cg_tol=1e-12 if precision == "f64" else 1e-7)
+    g.set_porosity(phi.astype(g.np_dtype))
+    g.init_state()
+    for _ in range(3):
+        g.step()
+    p = g.get_state("p")
+    c = 0.62 * (0.5 / (0.5 + 1e-10)) ** 2.5
+    dp = 1.225 * c * U * U * 10 * h
+    tol = 1e-9 if precision == "f64" else 2e-5
+    np.testing.assert_allclose(p[:, :, :15], dp, rtol=tol)
+    assert np.abs(p[:, :, 25:]).max() <= tol * dp
+    np.testing.assert_allclose(g.get_state("u"), U, rtol=tol)
+
+
+def test_objective_matches_oracle():
+    sc = ragged_urban()
+    o, g = pair(sc, "f64")
+    o.init()
+    o.run(5)
+    g.set_fields(o.state())
+    assert g.objective() == pytest.approx(o.objective(), rel=1e-12)
+    assert g.objective(0.0, 100.0, 2.0, 0.5) == pytest.approx(o.objective(0.0, 100.0, 2.0, 0.5), rel=1e-12)
+
+
+@pytest.mark.slow
+def test_full_size_urban_one_step_fp32():
+    """256 x 256 x 64 urban block (the benchmark workload), launch
+    configuration as timed: one step from a shared state, every field."""
+    sc = layouts.urban_block()
+    o, g = pair(sc, "f32")
+    o.init()
+    g.set_fields(o.state())
+    st = g.step()
+    o.step()
+    assert st.status == 0
+    for f in FIELDS6:
+        e = rel(g.get_state(f), o.get(f))
+        assert e <= 1e-5, (f, e)
+    assert g.divergence() <= 1e-6
+
+
+# ------------------------------------------------------- error paths ---
+
+def test_step_before_state_is_an_error():
+    g = uf.Grid(16, 8, 4)
+    with pytest.raises(uf.UFError) as ei:
+        g.step()
+    assert ei.value.status == uf.UF_ERR_STATE
+
+
+def test_iteration_cap_reports_not_converged():
+    sc = ragged_urban()
+    g = uf.Grid(sc.nx, sc.ny, sc.nz, **sc.params(), cg_max_iter=1)
+    g.set_porosity(sc.phi.astype(np.float32))
+    with pytest.raises(uf.UFError) as ei:
+        g.init_state()
+    assert ei.value.status == uf.UF_ERR_NOT_CONVERGED
+
+
+def test_nan_input_reports_nan():
+    """A NaN seeded on the host into the pressure warm start makes the CG
+    residual non-finite; the step returns UF_ERR_NAN instead of hanging."""
+    sc = ragged_urban()
+    g = uf.Grid(sc.nx, sc.ny, sc.nz, **sc.params())
+    g.init_state()
+    p = g.get_state("p")
+    p[3, 5, 7] = np.nan
+    g.set_state("p", p)
+    with pytest.raises(uf.UFError) as ei:
+        g.step()
+    assert ei.value.status == uf.UF_ERR_NAN
+    # the context stays usable
+    g.init_state()
+    assert g.step().status == 0
+
+
+def test_small_workspace_rejected():
+    lib = uf.load()
+    d = uf.default_desc()
+    need = uf.workspace_bytes(d)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    h = ctypes.c_void_p()
+    assert lib.uf_create_grid(ctypes.byref(d), ctypes.c_void_p(ws.data_ptr()), need - 4096,
+                              ctypes.c_void_p(s.cuda_stream), ctypes.byref(h)) == uf.UF_ERR_NOMEM
