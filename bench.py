@@ -1,0 +1,328 @@
+"""Benchmark: RANS cell-updates/s of the GB300 step on the 256 x 256 x 64 urban block.
+
+One "step" is one full time step of the hot path: CFL dt, eddy viscosity,
+MacCormack advection, diffusion, porosity drag + BCs, pressure right-hand
+side, MG-preconditioned CG pressure solve, projection and the k-omega
+update, FP32 fields with FP64 reductions.  Inputs are resident in HBM when the
+timed region starts.  The workload is the seeded synthetic urban block (40
+solid boxes + 60 porous canopies, seed = rank, log-law inflow 3 m/s at 10 m);
+its per-step working set (~400 MB) exceeds the 129 MB L2, so no flush is
+needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU: replicas only (each rank advances its own independent grid; no
+collective in the data path), weak scaling; rank 0 prints one JSON line.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RANS cell-updates/s at 256x256x64 FP32 (% HBM roofline); adjoint/forward time"
+UNIT = "cell-updates/s"
+NX, NY, NZ = 256, 256, 64
+
+
+def workload_config(extra=None):
+    cfg = {
+        "workload": "urban block 256x256x64, h=2 m, 40 solid boxes + 60 porous canopies (seeded), "
+                    "log-law inflow 3 m/s at 10 m, FP32 fields + FP64 reductions, MG-preconditioned CG",
+        "nx": NX, "ny": NY, "nz": NZ, "cells": NX * NY * NZ,
+        "l2": "no flush: per-step working set ~400 MB > 129 MB L2",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+        return False
+
+    def summary(self):
+        if not self.out:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2204_01117_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_label: str):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, or
+    None when the summary is missing or the kernel sources changed since."""
+    p = os.path.join(ROOT, "profiles", "mg_pcg_urban256.md")
+    if not os.path.exists(p):
+        return None
+    text = open(p).read()
+    m = re.search(r"source digest:\s*`([0-9a-f]+)`", text)
+    if not m or m.group(1) != source_digest():
+        return None
+    for line in text.splitlines():
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 3 and cells[0] == kernel_label:
+            try:
+                return float(cells[2])
+            except ValueError:
+                return None
+    return None
+
+
+# ---------------------------------------------------------------- oracle arm
+
+def oracle_sample(max_seconds: float = 150.0, steps_wanted: int = 1):
+    """Times the FP64 oracle (as it stands) on the full workload: untimed
+    initial projection, then timed oracle steps until `steps_wanted` or the
+    time cap.  Returns (cell-updates/s, cores, sample description, steps)."""
+    import oracle
+    from paper_2204_01117_gb300 import layouts
+    oracle.build()
+    sc = layouts.urban_block(NX, NY, NZ, seed=0)
+    o = oracle.Oracle(sc.nx, sc.ny, sc.nz, **sc.params())
+    o.set("phi", sc.phi)
+    o.init()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    done = 0
+    while done < max(1, steps_wanted):
+        o.step()
+        done += 1
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    dt = time.perf_counter() - t0
+    rate = sc.cells * done / dt
+    sample = (f"{done} FP64 oracle step(s) of the full 256x256x64 workload after its own initial "
+              f"projection (untimed); CG to ||r||/||b|| <= 1e-13; OpenMP threads={cores}")
+    return rate, cores, sample, done, dt
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    rate, cores, sample, done, dt = oracle_sample(max_seconds=150.0, steps_wanted=max(1, min(args.steps, 3)))
+    line = {
+        "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus, "steps": done,
+        "warmup": 0, "ms_per_step": dt / done * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": workload_config(),
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2204_01117_gb300 import layouts, uf
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    uf.build()
+    uf.load()
+    sc = layouts.urban_block(NX, NY, NZ, seed=rank)
+    g = uf.Grid(sc.nx, sc.ny, sc.nz, precision="f32", **sc.params())
+    g.set_porosity(sc.phi.astype(np.float32))
+    g.init_state()
+    for _ in range(max(args.warmup, 3)):
+        g.step(stats=False)
+    st0 = g.step()
+    fixed, per_iter = g.launch_counts()
+
+    s = g.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_index = vis.split(",")[local].strip() if vis else str(local)
+    with ClockSampler(smi_index) as clk:
+        e0.record(s)
+        for _ in range(args.steps):
+            g.step(stats=False)
+        e1.record(s)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st1 = g.step()
+    iters_timed = st1.cg_iters_total - st0.cg_iters_total - st1.cg_iters
+    launches = args.steps * fixed + iters_timed * per_iter
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = sc.cells * args.steps * world / (ms * 1e-3)
+
+    # -- end to end through the C ABI with pinned host buffers ------------
+    names = ("u", "v", "w", "p", "k", "omega")
+    host_in = {n: torch.from_numpy(g.get_state(n)).pin_memory() for n in names}
+    host_out = {n: torch.empty_like(host_in[n]).pin_memory() for n in names}
+    h2d = sum(t.numel() * 4 for t in host_in.values())
+    d2h = sum(t.numel() * 4 for t in host_out.values())
+    e2e_steps = max(3, min(args.steps, 10))
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for n in names:
+            g.set_state(n, host_in[n])
+        g.step(stats=False)
+        for n in names:
+            g.get_state(n, out=host_out[n])
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if pg:
+        t = torch.tensor([e2e_s], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = sc.cells * e2e_steps * world / e2e_s
+
+    # -- per-kernel CUDA-event timing of one eagerly launched step ----------
+    pst, kernels = g.profile_step()
+    dom_name, dom = max(kernels.items(), key=lambda kv: kv[1]["total_ms"])
+    avg_ms = dom["total_ms"] / dom["launches"]
+    achieved = dom["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    traffic = ncu_traffic(dom_name)
+    total_prof = sum(k["total_ms"] for k in kernels.values())
+
+    if rank != 0:
+        if pg:
+            pg.barrier()
+            pg.destroy_process_group()
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config({"parallelism": f"replicas x{world}", "cg_iters_last_step": st1.cg_iters,
+                                   "precond": "MG V-cycle (damped Jacobi 2+2)", "cg_tol": 1e-7}),
+        "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"hbm_gbs of {peak_kind}",
+                     "kernel_share_of_step": dom["total_ms"] / total_prof,
+                     "bytes_per_launch": dom["bytes_per_launch"], "avg_launch_us": avg_ms * 1e3},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline and world == 1:
+        rate, cores, sample, done, dt = oracle_sample(max_seconds=60.0, steps_wanted=1)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

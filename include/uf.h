@@ -106,6 +106,7 @@ typedef struct {
   int cg_iters;            /* CG iterations of the pressure solve            */
   double cg_rel_residual;  /* ||r||/||b|| at exit (recursive residual)      */
   int status;              /* uf_status of the device-side checks           */
+  long long cg_iters_total;/* CG iterations since the grid was created      */
 } uf_step_stats;
 
 /* Per-kernel timing of one profiled step (uf_profile_step). */
@@ -198,6 +199,12 @@ uf_status uf_profile_step(uf_grid* g, uf_kernel_time* out, int capacity, int* co
 /* Kernel launches per step of the captured graph, counting every CG
  * iteration of the last step; 0 before the first step. */
 int uf_last_step_launches(uf_grid* g);
+
+/* Kernel launches of one graph step: *fixed outside the CG loop (including
+ * the solver set-up) and *per_iter per CG iteration; with the cumulative
+ * iteration count of uf_step_stats this counts every kernel a run launched.
+ * Builds the step graphs if needed. */
+uf_status uf_launch_counts(uf_grid* g, int* fixed, int* per_iter);
 
 /* Thread-local message of the last failure. */
 const char* uf_last_error(void);

@@ -277,6 +277,7 @@ struct uf_grid {
   virtual uf_status apply_poisson(const void*, void*) = 0;
   virtual uf_status poisson_solve(const void*, int*, double*) = 0;
   virtual int last_launches() = 0;
+  virtual uf_status launch_counts(int*, int*) = 0;
   virtual uf_status profile_step(uf_kernel_time*, int, int*, uf_step_stats*) = 0;
 };
 
@@ -848,6 +849,7 @@ class GridImpl final : public uf_grid {
       out->cg_iters = h.iter;
       out->cg_rel_residual = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
       out->status = h.status;
+      out->cg_iters_total = h.total_iters;
     }
     if (h.sticky != 0) {
       const int code = h.sticky;
@@ -946,6 +948,14 @@ class GridImpl final : public uf_grid {
     return s;
   }
 
+  uf_status launch_counts(int* fixed, int* per_iter) override {
+    uf_status s = build_step_graphs();
+    if (s != UF_OK) return s;
+    if (fixed) *fixed = launches_fixed + launches_solve_setup;
+    if (per_iter) *per_iter = launches_per_iter;
+    return UF_OK;
+  }
+
   int last_launches() override {
     if (last_iters < 0) return 0;
     return launches_fixed + launches_solve_setup + last_iters * launches_per_iter;
@@ -1036,6 +1046,7 @@ uf_status uf_poisson_solve(uf_grid* g, const void* b, int* iters, double* rel) {
   return g->poisson_solve(b, iters, rel);
 }
 int uf_last_step_launches(uf_grid* g) { return g ? g->last_launches() : 0; }
+uf_status uf_launch_counts(uf_grid* g, int* fixed, int* per_iter) { UF_NEED(g); return g->launch_counts(fixed, per_iter); }
 uf_status uf_profile_step(uf_grid* g, uf_kernel_time* out, int capacity, int* count, uf_step_stats* stats) {
   UF_NEED(g);
   if (capacity < 0) return fail(UF_ERR_ARG, "negative capacity");

@@ -218,6 +218,7 @@ __global__ void __launch_bounds__(FT) k_mg_down(Level<T> F, Level<T> C, T omega,
         const double rr = tot[0];
         st->rr = rr;
         st->iter = it0 + 1;
+        st->total_iters += 1;
         if (!(rr == rr) || isinf(rr)) {
           st->status = DEV_NAN;
           if (st->sticky == 0) st->sticky = DEV_NAN;

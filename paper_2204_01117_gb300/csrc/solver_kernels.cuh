@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(NT) k_cg_update(Level<T> L, T* __restrict__ x,
       const double rr = tot[0];
       st->rr = rr;
       st->iter = it + 1;
+      st->total_iters += 1;
       if (!(rr == rr) || isinf(rr)) {
         st->status = DEV_NAN;
         if (st->sticky == 0) st->sticky = DEV_NAN;

@@ -360,6 +360,7 @@ struct SolveState {
   double bb, rr, rz, dq, alpha, beta, rr0, tol2;
   int iter, converged, status, max_iter, sticky;
   unsigned int ticket[4];
+  long long total_iters;   // CG iterations since the grid was created
 };
 
 template <typename T>

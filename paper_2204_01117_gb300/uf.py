@@ -55,7 +55,8 @@ class GridDesc(ctypes.Structure):
 
 class StepStats(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("cg_iters", ctypes.c_int),
-                ("cg_rel_residual", ctypes.c_double), ("status", ctypes.c_int)]
+                ("cg_rel_residual", ctypes.c_double), ("status", ctypes.c_int),
+                ("cg_iters_total", ctypes.c_longlong)]
 
 
 class KernelTime(ctypes.Structure):
@@ -129,6 +130,8 @@ def load():
     lib.uf_last_error.restype = ctypes.c_char_p
     lib.uf_profile_step.argtypes = [vp, P(KernelTime), ip, P(ip), P(StepStats)]
     lib.uf_profile_step.restype = ip
+    lib.uf_launch_counts.argtypes = [vp, P(ip), P(ip)]
+    lib.uf_launch_counts.restype = ip
     for name in ("uf_create_grid", "uf_destroy", "uf_set_porosity", "uf_set_state", "uf_get_state",
                  "uf_init_state", "uf_step", "uf_run", "uf_objective", "uf_divergence",
                  "uf_apply_poisson", "uf_poisson_solve"):
@@ -290,6 +293,13 @@ class Grid:
             out[k.name.decode()] = dict(launches=k.launches, total_ms=k.total_ms,
                                         bytes_per_launch=k.bytes_per_launch)
         return s, out
+
+    def launch_counts(self):
+        """(kernels per step outside the CG loop, kernels per CG iteration)."""
+        fixed = ctypes.c_int()
+        per = ctypes.c_int()
+        check(self.lib.uf_launch_counts(self._h, ctypes.byref(fixed), ctypes.byref(per)))
+        return fixed.value, per.value
 
     def launches_last_step(self) -> int:
         return int(self.lib.uf_last_step_launches(self._h))
