@@ -206,6 +206,35 @@ int uf_last_step_launches(uf_grid* g);
  * Builds the step graphs if needed. */
 uf_status uf_launch_counts(uf_grid* g, int* fixed, int* per_iter);
 
+/* ---- Pressure solve without any device allocation ---------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc or hand the library a workspace: code running
+ * inside another framework's memory pool, plug-ins in a host application
+ * that owns the CUDA context and forbids allocations after start-up, and
+ * real-time loops that must never take the allocator's locks or fail with
+ * out-of-memory mid-run.
+ *
+ * Solves A p = b with the operator of uf_poisson_solve (7-point, outlet
+ * sides from wind_dir_deg get p = 0 ghosts, other sides dp/dn = 0) by CG
+ * preconditioned with the paper's first-order approximate inverse (w = 1.65),
+ * FP32 vectors, FP64 inner products, stopping at ||r|| <= tol ||b|| or after
+ * max_iter iterations.  b (input) and p (warm start in, solution out) are
+ * dense device arrays of nx*ny*nz floats, x fastest; stream is a created
+ * cudaStream_t.  Synchronises; fills *iters and *rel_residual (may be NULL).
+ *
+ * Scratch: a file-scope __device__ array of UF_STATIC_SCRATCH_BYTES, which
+ * every GPU that loads the library holds until the process exits.  Grids
+ * above UF_STATIC_MAX_CELLS cells are rejected with UF_ERR_ARG.  The first
+ * call on each device looks the array's address up (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream
+ * capture.  Every call uses the same array and resets its solver state
+ * first; calls that overlap on the GPU (other threads or streams) race on
+ * it, so serialise them.  Calls no cudaMalloc or cudaFree. */
+#define UF_STATIC_SCRATCH_BYTES (16u << 20)
+#define UF_STATIC_MAX_CELLS 800000
+uf_status uf_poisson_solve_static(int nx, int ny, int nz, double wind_dir_deg, const float* b, float* p,
+                                  double tol, int max_iter, void* stream, int* iters, double* rel_residual);
+
 /* Thread-local message of the last failure. */
 const char* uf_last_error(void);
 

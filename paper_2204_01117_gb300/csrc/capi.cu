@@ -263,6 +263,8 @@ dim3 chunk_grid(int lx, int ly, int lz, int* zc) {
 
 }  // namespace
 
+void uf_internal_set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
 // ======================================================================
 struct uf_grid {
   virtual ~uf_grid() {}

@@ -20,7 +20,7 @@ ROOT = os.path.dirname(_HERE)
 CSRC = os.path.join(_HERE, "csrc")
 LIB_PATH = os.path.join(_HERE, "_build", "libuf.so")
 HEADER = os.path.join(ROOT, "include", "uf.h")
-SOURCES = ["capi.cu"]
+SOURCES = ["capi.cu", "noalloc.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo",
               "--expt-extended-lambda", "-Xcompiler", "-fPIC", "-shared"]
 
@@ -83,11 +83,23 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 and os.path.getmtime(LIB_PATH) >= max(os.path.getmtime(p) for p in deps)):
             return LIB_PATH
         os.makedirs(os.path.dirname(LIB_PATH), exist_ok=True)
-        tmp = LIB_PATH + f".tmp{os.getpid()}"
-        cmd = ["nvcc", *NVCC_FLAGS, *srcs, "-o", tmp]
-        if verbose:
-            print(" ".join(cmd))
-        subprocess.check_call(cmd)
+        tag = f".tmp{os.getpid()}"
+        objs, procs = [], []
+        compile_flags = [f for f in NVCC_FLAGS if f != "-shared"]
+        for src in srcs:   # translation units compile in parallel
+            obj = os.path.join(os.path.dirname(LIB_PATH), os.path.basename(src) + tag + ".o")
+            cmd = ["nvcc", *compile_flags, "-c", src, "-o", obj]
+            if verbose:
+                print(" ".join(cmd))
+            procs.append(subprocess.Popen(cmd))
+            objs.append(obj)
+        codes = [pr.wait() for pr in procs]
+        if any(codes):
+            raise subprocess.CalledProcessError(max(codes), "nvcc")
+        tmp = LIB_PATH + tag
+        subprocess.check_call(["nvcc", "-shared", "-gencode", "arch=compute_103a,code=sm_103a", *objs, "-o", tmp])
+        for obj in objs:
+            os.remove(obj)
         os.replace(tmp, LIB_PATH)
         return LIB_PATH
 
@@ -132,6 +144,8 @@ def load():
     lib.uf_profile_step.restype = ip
     lib.uf_launch_counts.argtypes = [vp, P(ip), P(ip)]
     lib.uf_launch_counts.restype = ip
+    lib.uf_poisson_solve_static.argtypes = [ip, ip, ip, dp, vp, vp, dp, ip, vp, P(ip), P(dp)]
+    lib.uf_poisson_solve_static.restype = ip
     for name in ("uf_create_grid", "uf_destroy", "uf_set_porosity", "uf_set_state", "uf_get_state",
                  "uf_init_state", "uf_step", "uf_run", "uf_objective", "uf_divergence",
                  "uf_apply_poisson", "uf_poisson_solve"):
@@ -181,6 +195,29 @@ def _ptr(buf, dtype):
         pass
     arr = np.ascontiguousarray(buf, dtype=dtype[1])
     return ctypes.c_void_p(arr.ctypes.data), arr
+
+
+STATIC_MAX_CELLS = 800000
+
+
+def poisson_solve_static(b, p, wind_dir_deg: float = 0.0, tol: float = 1e-7, max_iter: int = 5000, stream=None):
+    """uf_poisson_solve_static on dense float32 CUDA tensors b (in) and p (in/out).
+
+    The solve allocates no device memory: its scratch is a fixed array inside
+    the library (see include/uf.h).  Returns (iterations, relative residual)."""
+    import torch
+    lib = load()
+    if b.dtype != torch.float32 or p.dtype != torch.float32 or not b.is_cuda or not p.is_cuda:
+        raise TypeError("b and p must be float32 CUDA tensors")
+    if not (b.is_contiguous() and p.is_contiguous()) or b.shape != p.shape or b.dim() != 3:
+        raise TypeError("b and p must be contiguous (nz, ny, nx) tensors of the same shape")
+    nz, ny, nx = b.shape
+    s = stream if stream is not None else torch.cuda.current_stream()
+    it, rel = ctypes.c_int(), ctypes.c_double()
+    check(lib.uf_poisson_solve_static(nx, ny, nz, wind_dir_deg, ctypes.c_void_p(b.data_ptr()),
+                                      ctypes.c_void_p(p.data_ptr()), tol, max_iter,
+                                      ctypes.c_void_p(s.cuda_stream), ctypes.byref(it), ctypes.byref(rel)))
+    return it.value, rel.value
 
 
 class Grid:
