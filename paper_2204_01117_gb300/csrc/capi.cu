@@ -41,7 +41,7 @@ int pitch_of(int lx) { return (int)round_up((size_t)lx, 32); }
 constexpr int kPartials = 8192;      // doubles per partials buffer
 constexpr int kDtBlocks = 1024;
 constexpr int kTargetBlocks = 2048;  // blocks of reducing cell kernels
-constexpr size_t kTailSmemBudget = 200 * 1024;
+constexpr size_t kTailSmemBudget = 64 * 1024;
 
 struct LevelDims {
   int nx, ny, nz, P;
@@ -113,7 +113,7 @@ struct Plan {
   size_t tail_smem;        // its dynamic shared memory (bytes)
   std::vector<int> tail_off;
   std::vector<size_t> lr, lx, lt;
-  size_t prof, dt, scal, state, partials, ainv;
+  size_t prof, dt, dtT, scal, state, partials, ainv;
   size_t total;
 };
 
@@ -177,6 +177,7 @@ Plan make_plan(const uf_grid_desc* d) {
   }
   P.prof = L.take((size_t)d->nz * tb);
   P.dt = L.take(8);
+  P.dtT = L.take(8);
   P.scal = L.take(8 * 8);
   P.state = L.take(sizeof(uf::SolveState));
   P.partials = L.take(sizeof(double) * kPartials * 2);
@@ -297,6 +298,7 @@ class GridImpl final : public uf_grid {
   T *u, *v, *w, *uh, *vh, *wh, *ut, *vt, *wt, *kb[2], *ob[2], *cc, *phi, *nut, *p, *b, *r, *r2, *z, *q, *d0, *d1, *prof;
   uf::TailArgs<T> tail;
   double *dt, *scal, *partials, *ainv;
+  T* dtT;
   uf::SolveState* st;
   cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
   cudaGraphExec_t init_exec = nullptr, solve_exec = nullptr;
@@ -330,7 +332,7 @@ class GridImpl final : public uf_grid {
     cc = at<T>(P.cc); phi = at<T>(P.phi); nut = at<T>(P.nut); p = at<T>(P.p); b = at<T>(P.b);
     r = at<T>(P.r); r2 = at<T>(P.r2); z = at<T>(P.z); q = at<T>(P.q); d0 = at<T>(P.d0); d1 = at<T>(P.d1);
     prof = at<T>(P.prof);
-    dt = at<double>(P.dt); scal = at<double>(P.scal); partials = at<double>(P.partials);
+    dt = at<double>(P.dt); dtT = at<T>(P.dtT); scal = at<double>(P.scal); partials = at<double>(P.partials);
     ainv = at<double>(P.ainv);
     st = at<uf::SolveState>(P.state);
     UF_CUDA(cudaMemsetAsync(ws, 0, P.total - 256, stream));
@@ -355,12 +357,15 @@ class GridImpl final : public uf_grid {
     sp.om_in = (T)(std::sqrt(kin) / (std::pow(d.C_mu, 0.25) * d.L));
     sp.prof = prof;
     sp.dt = dt;
+    sp.dtT = dtT;
     std::vector<T> hp(d.nz);
     for (int k = 0; k < d.nz; ++k) hp[k] = (T)inflow_speed(d, (k + 0.5) * d.h);
     UF_CUDA(cudaMemcpyAsync(prof, hp.data(), sizeof(T) * d.nz, cudaMemcpyHostToDevice, stream));
     if (d.fixed_dt > 0) {
       const double fdt = d.fixed_dt;
+      const T fdtT = (T)d.fixed_dt;
       UF_CUDA(cudaMemcpyAsync(dt, &fdt, sizeof(double), cudaMemcpyHostToDevice, stream));
+      UF_CUDA(cudaMemcpyAsync(dtT, &fdtT, sizeof(T), cudaMemcpyHostToDevice, stream));
     }
     // solver constants
     uf::SolveState s0;
@@ -457,31 +462,25 @@ class GridImpl final : public uf_grid {
   double Nl(int l) const { return (double)lv[l].nx * lv[l].ny * lv[l].nz; }
   double tb() const { return (double)sizeof(T); }
 
-  size_t down_smem() const { return (uf::H2N + uf::H1N + uf::TN) * sizeof(T); }
-  size_t up_smem() const { return (uf::H2N + uf::H1N) * sizeof(T); }
-  size_t dirq_smem() const { return uf::H1N * sizeof(T); }
 
   cudaError_t set_smem_limits() {
     cudaError_t e = cudaSuccess;
     auto lim = [&](const void* f, size_t bytes) {
       if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     };
-    lim((const void*)uf::k_mg_down<T, uf::SM_JACOBI, true>, down_smem());
-    lim((const void*)uf::k_mg_down<T, uf::SM_JACOBI, false>, down_smem());
-    lim((const void*)uf::k_mg_down<T, uf::SM_RBGS, true>, down_smem());
-    lim((const void*)uf::k_mg_down<T, uf::SM_RBGS, false>, down_smem());
-    lim((const void*)uf::k_mg_up<T, uf::SM_JACOBI, true>, up_smem());
-    lim((const void*)uf::k_mg_up<T, uf::SM_JACOBI, false>, up_smem());
-    lim((const void*)uf::k_mg_up<T, uf::SM_RBGS, true>, up_smem());
-    lim((const void*)uf::k_mg_up<T, uf::SM_RBGS, false>, up_smem());
     lim((const void*)uf::k_mg_tail<T, uf::SM_JACOBI>, std::max<size_t>(P.tail_smem, 1));
     lim((const void*)uf::k_mg_tail<T, uf::SM_RBGS>, std::max<size_t>(P.tail_smem, 1));
-    lim((const void*)uf::k_cg_dir_q<T>, dirq_smem());
     return e;
   }
 
-  static dim3 tile_grid(const uf::Level<T>& L) {
-    return dim3((L.nx + uf::TX - 1) / uf::TX, (L.ny + uf::TY - 1) / uf::TY, (L.nz + uf::TZ - 1) / uf::TZ);
+  // z-marching grid: 32 x 8 columns, zc planes (even) per block, zc chosen
+  // so that the level still gives a few blocks per SM.
+  static dim3 march_grid(const uf::Level<T>& L, int* zc) {
+    const int bx = (L.nx + uf::TX - 1) / uf::TX, by = (L.ny + uf::TY - 1) / uf::TY;
+    int z = 16;
+    while (z > 2 && (long)bx * by * ((L.nz + z - 1) / z) < 456) z /= 2;
+    *zc = z;
+    return dim3(bx, by, (L.nz + z - 1) / z);
   }
 
   // Fused V-cycle: down kernels to the tail level, the tail, up kernels.
@@ -493,30 +492,32 @@ class GridImpl final : public uf_grid {
     const int lt = P.tail_level;
     for (int l = 0; l < lt; ++l) {
       const std::string sl = std::to_string(l);
-      const dim3 g = tile_grid(lv[l]);
+      int zc;
+      const dim3 g = march_grid(lv[l], &zc);
       if (l == 0 && mode == 1)
         L(s, "mg_down_cg_L0", (7 * Nl(0) + Nl(1)) * tb(), [&] {
-          uf::k_mg_down<T, SM, true><<<g, uf::FT, down_smem(), s>>>(lv[0], lv[1], om, p, d0, d1, q, partials, st,
-                                                                   cond, use_cond);
+          uf::k_mg_down<T, SM, true><<<g, uf::FT, 0, s>>>(lv[0], lv[1], om, zc, p, d0, d1, q, partials, st, cond,
+                                                         use_cond);
         });
       else
         L(s, "mg_down_L" + sl, (2 * Nl(l) + Nl(l + 1)) * tb(), [&] {
-          uf::k_mg_down<T, SM, false><<<g, uf::FT, down_smem(), s>>>(lv[l], lv[l + 1], om, nullptr, nullptr, nullptr,
-                                                                    nullptr, partials, st, cond, 0);
+          uf::k_mg_down<T, SM, false><<<g, uf::FT, 0, s>>>(lv[l], lv[l + 1], om, zc, nullptr, nullptr, nullptr,
+                                                          nullptr, partials, st, cond, 0);
         });
     }
     L(s, "mg_tail", (double)P.coarse_n * P.coarse_n * 8 + 2 * Nl(lt) * tb(),
       [&] { uf::k_mg_tail<T, SM><<<1, uf::TAIL_T, P.tail_smem, s>>>(tail, om, st); });
     for (int l = lt - 1; l >= 0; --l) {
       const std::string sl = std::to_string(l);
-      const dim3 g = tile_grid(lv[l]);
+      int zc;
+      const dim3 g = march_grid(lv[l], &zc);
       if (l == 0)
         L(s, "mg_up_L0", (3 * Nl(0) + Nl(1)) * tb(), [&] {
-          uf::k_mg_up<T, SM, true><<<g, uf::FT, up_smem(), s>>>(lv[0], lv[1], om, z, mode, partials, st);
+          uf::k_mg_up<T, SM, true><<<g, uf::FT, 0, s>>>(lv[0], lv[1], om, zc, z, mode, partials, st);
         });
       else
         L(s, "mg_up_L" + sl, (3 * Nl(l) + Nl(l + 1)) * tb(), [&] {
-          uf::k_mg_up<T, SM, false><<<g, uf::FT, up_smem(), s>>>(lv[l], lv[l + 1], om, lv[l].t, mode, partials, st);
+          uf::k_mg_up<T, SM, false><<<g, uf::FT, 0, s>>>(lv[l], lv[l + 1], om, zc, lv[l].t, mode, partials, st);
         });
     }
   }
@@ -549,8 +550,10 @@ class GridImpl final : public uf_grid {
   }
   void rec_cg_iter(cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
     if (d.precond == UF_PRECOND_MG) {
+      int zc;
+      const dim3 g = march_grid(lv[0], &zc);
       L(s, "cg_dir_q", 4 * N() * tb(), [&] {
-        uf::k_cg_dir_q<T><<<tile_grid(lv[0]), uf::FT, dirq_smem(), s>>>(lv[0], z, d0, d1, q, partials, st);
+        uf::k_cg_dir_q<T><<<g, uf::FT, 0, s>>>(lv[0], zc, z, d0, d1, q, partials, st);
       });
       rec_vcycle(s, 1, cond, use_cond);
       return;
@@ -621,7 +624,7 @@ class GridImpl final : public uf_grid {
     A.Lv = {d.nx, d.ny + 1, d.nz, P.Pc};
     A.Lw = {d.nx, d.ny, d.nz + 1, P.Pc};
     A.nx = d.nx; A.ny = d.ny; A.nz = d.nz;
-    A.dt = dt;
+    A.dtT = dtT;
     A.inv_h = (T)(1.0 / d.h);
     return A;
   }
@@ -631,7 +634,7 @@ class GridImpl final : public uf_grid {
     const double faces = 3 * N() * tb(), cells = N() * tb();
     if (!(d.fixed_dt > 0))
       L(s, "cfl_dt", faces, [&] {
-        uf::k_cfl_dt<T><<<kDtBlocks, 256, 0, s>>>(u, P.n_u, v, P.n_v, w, P.n_w, d.cfl * d.h, partials, &st->ticket[0], dt);
+        uf::k_cfl_dt<T><<<kDtBlocks, 256, 0, s>>>(u, P.n_u, v, P.n_v, w, P.n_w, d.cfl * d.h, partials, &st->ticket[0], dt, dtT);
       });
     L(s, "eddy_viscosity", faces + 3 * cells,
       [&] { uf::k_eddy_viscosity<T><<<plane_grid(d.nx, d.ny, d.nz), blk, 0, s>>>(sp, u, v, w, kin, oin, nut); });
@@ -812,7 +815,7 @@ class GridImpl final : public uf_grid {
         uf::k_init_fields<T><<<ga, blk, 0, s>>>(sp, u, v, w, kb[0], ob[0], p);
         rec_count++;
         if (!(d.fixed_dt > 0)) {
-          uf::k_cfl_dt<T><<<kDtBlocks, 256, 0, s>>>(u, P.n_u, v, P.n_v, w, P.n_w, d.cfl * d.h, partials, &st->ticket[0], dt);
+          uf::k_cfl_dt<T><<<kDtBlocks, 256, 0, s>>>(u, P.n_u, v, P.n_v, w, P.n_w, d.cfl * d.h, partials, &st->ticket[0], dt, dtT);
           rec_count++;
         }
         uf::k_drag_bc<T><<<ga, blk, 0, s>>>(sp, u, v, w, cc, uh, vh, wh);

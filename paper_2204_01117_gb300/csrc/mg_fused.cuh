@@ -5,6 +5,7 @@
 // shared memory, so that two dependent smoothing passes and the residual run
 // without another trip to global memory:
 //
+//   (k_mg_down, k_mg_up and k_cg_dir_q march along z with rolling planes.)
 //   k_mg_down  : [finest level: CG update x += a d, r -= a q, ||r||^2]
 //                pre-smoothing from a zero guess, residual, summed
 //                restriction to the next level.            reads r (q, x, d)
@@ -80,6 +81,37 @@ __device__ __forceinline__ PlaneMap plane_map() {
   return m;
 }
 
+// Per-thread precomputation for a plane position (x, y) of a staged region
+// with origin (ox, oy): x-y validity, 32-bit offset within a z plane, and
+// the x-y part of the diagonal; per plane only the z terms remain.
+template <typename T>
+struct PosXY {
+  bool ok;
+  int off;
+  T dxy;
+};
+template <typename T>
+__device__ __forceinline__ PosXY<T> pos_xy(const Level<T>& L, int gx, int gy) {
+  PosXY<T> r;
+  r.ok = gx >= 0 && gy >= 0 && gx < L.nx && gy < L.ny;
+  r.off = r.ok ? gx + L.P * gy : 0;
+  T D = T(2) * (L.wx + L.wy);
+  if (gx == 0 && !(L.out_mask & 1)) D -= L.wx;
+  if (gx == L.nx - 1 && !(L.out_mask & 2)) D -= L.wx;
+  if (gy == 0 && !(L.out_mask & 4)) D -= L.wy;
+  if (gy == L.ny - 1 && !(L.out_mask & 8)) D -= L.wy;
+  r.dxy = D;
+  return r;
+}
+// z part of the diagonal for plane k.
+template <typename T>
+__device__ __forceinline__ T diag_z(const Level<T>& L, int k) {
+  T D = T(2) * L.wz;
+  if (k == 0 && !(L.out_mask & 16)) D -= L.wz;
+  if (k == L.nz - 1 && !(L.out_mask & 32)) D -= L.wz;
+  return D;
+}
+
 // Pre-smoothing from zero with q = r/D staged: Jacobi x2 = w(2-w) q_c +
 // w^2/D_c sum w_a q_nb;  RBGS red q_c, black q_c + sum w_a q_nb / D_c.
 template <int SM, typename T>
@@ -96,19 +128,33 @@ __device__ __forceinline__ T relax(T tc, T rc, T s, T D, T omega, bool active) {
 }
 
 // ------------------------------------------------------------ down -------
+// Blocks own a 32 x 8 column of cells and march along z over `zc` planes
+// (zc even), keeping rolling planes in shared memory: q = r/D on the tile
+// plus a halo of 2 (ring of 4 planes), the pre-smoothed x on the tile plus a
+// halo of 1 (ring of 3), and the residual of the current z pair.  Per plane:
+// load q(k+2); pre-smooth x(k+1); residual of plane k; after every pair of
+// planes, restrict it.  CG = true (finest level inside the CG loop): the
+// kernel first applies x += alpha d, r -= alpha q (r ping-pongs), reduces
+// ||r||^2 and runs the convergence test.
+constexpr int QX = TX + 4, QY = TY + 4, QP = QX * QY;   // 36 x 12 plane (halo 2)
+constexpr int XX = TX + 2, XY = TY + 2, XP = XX * XY;   // 34 x 10 plane (halo 1)
+
+__device__ __forceinline__ int ring3(int k) { return ((k % 3) + 3) % 3; }
+__device__ __forceinline__ int ring4(int k) { return (k + 4) & 3; }
+
 template <typename T, int SM, bool CG>
-__global__ void __launch_bounds__(FT) k_mg_down(Level<T> F, Level<T> C, T omega, T* __restrict__ x,
+__global__ void __launch_bounds__(FT) k_mg_down(Level<T> F, Level<T> C, T omega, int zc, T* __restrict__ x,
                                                const T* d0, const T* d1, const T* __restrict__ q,
                                                double* partials, SolveState* st, cudaGraphConditionalHandle cond,
                                                int use_cond) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Sq = reinterpret_cast<T*>(smem_raw);   // H2N: r/D on tile + halo 2 (0 outside)
-  T* Sx = Sq + H2N;                          // H1N: pre-smoothed x on tile + halo 1 (0 outside)
-  T* Ss = Sx + H1N;                          // TN : fine residual of owned cells
+  __shared__ T sQ[4][QP];
+  __shared__ T sX[3][XP];
+  __shared__ T sR[2][FT];
   __shared__ double sh[32];
   __shared__ bool last;
   if (!CG && st->converged) return;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * TZ;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * zc;
+  const int kend = min(F.nz, k0 + zc);
   const int tid = threadIdx.x, tx = tid & (TX - 1), ty = tid / TX;
   const int it0 = st->iter;
   const T* r_in = level_r(F, it0);
@@ -119,96 +165,146 @@ __global__ void __launch_bounds__(FT) k_mg_down(Level<T> F, Level<T> C, T omega,
     dn = (it0 & 1) ? d0 : d1;
     alpha = (T)st->alpha;
   }
-  // 1. q = r/D (CG-updated r on the finest level) on tile + halo 2
-  {
-    const PlaneMap m = plane_map<H2X, H2Y>();
-#pragma unroll 2
-    for (int ez = 0; ez < H2Z; ++ez) {
-      const int gk = k0 - 2 + ez;
+  const size_t PS = (size_t)F.P * F.ny;   // z-plane stride
+  // per-thread positions: two in the halo-2 plane, two in the halo-1 plane
+  const PlaneMap mq = plane_map<QX, QY>();
+  const PlaneMap mx = plane_map<XX, XY>();
+  PosXY<T> pq[2], px[2];
+  int sq[2], sx[2], sxq[2], par[2];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (h == 1 && !m.has1) break;
-        const int ex = h ? m.x1 : m.x0, ey = h ? m.y1 : m.y0;
-        const int gi = i0 - 2 + ex, gj = j0 - 2 + ey;
-        T v = 0;
-        if (in_level(F, gi, gj, gk)) {
-          const size_t c = lidx(F, gi, gj, gk);
-          T rv = r_in[c];
-          if (CG) rv -= alpha * q[c];
-          v = rv / diag_of(F, gi, gj, gk);
-        }
-        Sq[ex + H2X * ey + H2P * ez] = v;
-      }
-    }
+  for (int h = 0; h < 2; ++h) {
+    const int qx = h ? mq.x1 : mq.x0, qy = h ? mq.y1 : mq.y0;
+    pq[h] = pos_xy(F, i0 - 2 + qx, j0 - 2 + qy);
+    if (h == 1 && !mq.has1) pq[h].ok = false;
+    sq[h] = qx + QX * qy;
+    const int xx = h ? mx.x1 : mx.x0, xy = h ? mx.y1 : mx.y0;
+    px[h] = pos_xy(F, i0 - 1 + xx, j0 - 1 + xy);
+    if (h == 1 && !mx.has1) px[h].ok = false;
+    sx[h] = xx + XX * xy;
+    sxq[h] = (xx + 1) + QX * (xy + 1);
+    par[h] = (i0 - 1 + xx + j0 - 1 + xy) & 1;
   }
   const int gi = i0 + tx, gj = j0 + ty;
-  const bool col_in = gi < F.nx && gj < F.ny;
+  const PosXY<T> po = pos_xy(F, gi, gj);
+  const int opar = (gi + gj) & 1;
+  // q-plane staging: a load stage (global -> registers) and a commit stage
+  // (registers -> shared), one iteration apart, so that the loads of plane
+  // k+3 are in flight while planes k+1 and k are processed.
+  T pr[2], pqv[2];
+  auto issueQ = [&](int k) {
+    const bool kin = (unsigned)k < (unsigned)F.nz;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      pr[h] = 0;
+      pqv[h] = 0;
+      if (kin && pq[h].ok) {
+        const size_t c = (size_t)k * PS + pq[h].off;
+        pr[h] = r_in[c];
+        if (CG) pqv[h] = q[c];
+      }
+    }
+  };
+  auto commitQ = [&](int k) {
+    T* dst = sQ[ring4(k)];
+    const bool kin = (unsigned)k < (unsigned)F.nz;
+    const T dz = diag_z(F, k);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && !mq.has1) break;
+      dst[sq[h]] = (kin && pq[h].ok) ? (CG ? pr[h] - alpha * pqv[h] : pr[h]) / (pq[h].dxy + dz) : T(0);
+    }
+  };
+  auto computeX = [&](int k) {
+    T* dst = sX[ring3(k)];
+    const T* qm = sQ[ring4(k - 1)];
+    const T* qc = sQ[ring4(k)];
+    const T* qp = sQ[ring4(k + 1)];
+    const bool kin = (unsigned)k < (unsigned)F.nz;
+    const T dz = diag_z(F, k);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && !mx.has1) break;
+      T v = 0;
+      if (kin && px[h].ok) {
+        const int b = sxq[h];
+        const T s = F.wx * (qc[b - 1] + qc[b + 1]) + F.wy * (qc[b - QX] + qc[b + QX]) + F.wz * (qm[b] + qp[b]);
+        v = presmooth<SM>(qc[b], s, px[h].dxy + dz, omega, ((par[h] + k) & 1) == 0);
+      }
+      dst[sx[h]] = v;
+    }
+  };
+  const int fx = F.cx ? 2 : 1, fy = F.cy ? 2 : 1;
+  const int cnx = TX / fx, cny = TY / fy;
   double acc = 0.0;
-  if (CG && col_in) {   // owned cells: r and x updates, ||r||^2
-#pragma unroll
-    for (int z = 0; z < TZ; ++z) {
-      const int gk = k0 + z;
-      if (gk < F.nz) {
-        const size_t c = lidx(F, gi, gj, gk);
-        const T rv = r_in[c] - alpha * q[c];
-        r_out[c] = rv;
-        x[c] += alpha * dn[c];
-        acc += (double)rv * (double)rv;
-      }
-    }
-  }
+  DotAcc<T> dacc;
+
+  issueQ(k0 - 2); commitQ(k0 - 2);
+  issueQ(k0 - 1); commitQ(k0 - 1);
+  issueQ(k0); commitQ(k0);
+  issueQ(k0 + 1);
   __syncthreads();
-  // 2. pre-smoothed x on tile + halo 1
-  {
-    const PlaneMap m = plane_map<H1X, H1Y>();
-#pragma unroll 2
-    for (int ez = 0; ez < H1Z; ++ez) {
-      const int gk = k0 - 1 + ez;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (h == 1 && !m.has1) break;
-        const int ex = h ? m.x1 : m.x0, ey = h ? m.y1 : m.y0;
-        const int hi = i0 - 1 + ex, hj = j0 - 1 + ey;
-        T v = 0;
-        if (in_level(F, hi, hj, gk)) {
-          const int b = (ex + 1) + H2X * (ey + 1) + H2P * (ez + 1);
-          v = presmooth<SM>(Sq[b], nbs<T, H2X, H2P>(F, Sq, b), diag_of(F, hi, hj, gk), omega,
-                            ((hi + hj + gk) & 1) == 0);
-        }
-        Sx[ex + H1X * ey + H1P * ez] = v;
-      }
-    }
-  }
+  computeX(k0 - 1);
+  commitQ(k0 + 1);
+  issueQ(k0 + 2);
   __syncthreads();
-  // 3. owned cells: store x_pre; residual r - A x = D (q - x) + sum w x_nb
-#pragma unroll
-  for (int z = 0; z < TZ; ++z) {
-    const int gk = k0 + z;
+  computeX(k0);
+  __syncthreads();
+  // a z-coarsened level of odd extent ends on a pair whose second plane is
+  // outside the domain (its residual is zero)
+  const int klast = (F.cz && (kend & 1)) ? kend + 1 : kend;
+  const int b1 = (tx + 1) + XX * (ty + 1);
+  const int b2 = (tx + 2) + QX * (ty + 2);
+  for (int k = k0; k < klast; ++k) {
+    const bool own = po.ok && k < F.nz;
+    // owned-cell operands of this plane, loaded ahead of the barriers
+    T o_r = 0, o_q = 0, o_x = 0, o_d = 0;
+    const size_t oc = (size_t)k * PS + po.off;
+    if (CG && own) {
+      o_r = r_in[oc];
+      o_q = q[oc];
+      o_x = x[oc];
+      o_d = dn[oc];
+    }
+    commitQ(k + 2);
+    issueQ(k + 3);
+    __syncthreads();
+    computeX(k + 1);
+    __syncthreads();
     T res = 0;
-    if (col_in && gk < F.nz) {
-      const int b1 = (tx + 1) + H1X * (ty + 1) + H1P * (z + 1);
-      const int b2 = (tx + 2) + H2X * (ty + 2) + H2P * (z + 2);
-      const T xc = Sx[b1];
-      F.x[lidx(F, gi, gj, gk)] = xc;
-      res = diag_of(F, gi, gj, gk) * (Sq[b2] - xc) + nbs<T, H1X, H1P>(F, Sx, b1);
+    if (own) {
+      const T* xm = sX[ring3(k - 1)];
+      const T* xc = sX[ring3(k)];
+      const T* xp = sX[ring3(k + 1)];
+      const T xv = xc[b1];
+      F.x[oc] = xv;
+      res = (po.dxy + diag_z(F, k)) * (sQ[ring4(k)][b2] - xv) + F.wx * (xc[b1 - 1] + xc[b1 + 1]) +
+            F.wy * (xc[b1 - XX] + xc[b1 + XX]) + F.wz * (xm[b1] + xp[b1]);
+      if (CG) {
+        const T rv = o_r - alpha * o_q;
+        r_out[oc] = rv;
+        x[oc] = o_x + alpha * o_d;
+        dacc.add(rv, rv);
+      }
     }
-    Ss[tx + TX * (ty + TY * z)] = res;
-  }
-  __syncthreads();
-  // 4. restriction: coarse cells of this tile sum their children in order
-  const int fx = F.cx ? 2 : 1, fy = F.cy ? 2 : 1, fz = F.cz ? 2 : 1;
-  const int cnx = TX / fx, cny = TY / fy, cnz = TZ / fz;
-  for (int e = tid; e < cnx * cny * cnz; e += FT) {
-    const int cxl = e % cnx, cyl = (e / cnx) % cny, czl = e / (cnx * cny);
-    const int ci = i0 / fx + cxl, cj = j0 / fy + cyl, ck = k0 / fz + czl;
-    if (!in_level(C, ci, cj, ck)) continue;
-    T s = 0;
-    for (int dz = 0; dz < fz; ++dz)
-      for (int dy = 0; dy < fy; ++dy)
-        for (int dx = 0; dx < fx; ++dx) s += Ss[(cxl * fx + dx) + TX * ((cyl * fy + dy) + TY * (czl * fz + dz))];
-    C.r[lidx(C, ci, cj, ck)] = s;
+    (void)opar;
+    sR[k & 1][tid] = res;
+    if (!F.cz || (k & 1)) {
+      __syncthreads();
+      const int kc = F.cz ? (k >> 1) : k;
+      for (int e = tid; e < cnx * cny; e += FT) {
+        const int cxl = e % cnx, cyl = e / cnx;
+        const int ci = i0 / fx + cxl, cj = j0 / fy + cyl;
+        if (!in_level(C, ci, cj, kc)) continue;
+        T sum = 0;
+        for (int dz = F.cz ? 1 : 0; dz >= 0; --dz)
+          for (int dy = 0; dy < fy; ++dy)
+            for (int dx = 0; dx < fx; ++dx) sum += sR[(k - dz) & 1][(cxl * fx + dx) + TX * (cyl * fy + dy)];
+        C.r[lidx(C, ci, cj, kc)] = sum;
+      }
+    }
   }
   if (CG) {
+    acc += dacc.value();
     acc = block_sum<FT>(acc, sh);
     const double vals[1] = {acc};
     if (publish_partials<1>(partials, &st->ticket[3], vals, &last)) {
@@ -238,79 +334,131 @@ __global__ void __launch_bounds__(FT) k_mg_down(Level<T> F, Level<T> C, T omega,
 }
 
 // -------------------------------------------------------------- up -------
-// t = x_pre + e(parent); two post-smoothing passes; output to `out`
-// (F.t on coarse levels, z on the finest).  FINEST: also r.z, beta.
+// Same z-march: t = x_pre + e(parent) on tile + halo 2 (ring of 4), first
+// post-smoothing pass on tile + halo 1 (ring of 3), second pass on the owned
+// plane, written to `out` (F.t on coarse levels, z on the finest).
+// FINEST: also r.z and the CG beta.  Global loads run one plane ahead.
 template <typename T, int SM, bool FINEST>
-__global__ void __launch_bounds__(FT) k_mg_up(Level<T> F, Level<T> C, T omega, T* __restrict__ out, int mode,
+__global__ void __launch_bounds__(FT) k_mg_up(Level<T> F, Level<T> C, T omega, int zc, T* __restrict__ out, int mode,
                                              double* partials, SolveState* st) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* St = reinterpret_cast<T*>(smem_raw);   // H2N: corrected x on tile + halo 2 (0 outside)
-  T* Su = St + H2N;                          // H1N: after the first pass (0 outside)
+  __shared__ T sT[4][QP];
+  __shared__ T sU[3][XP];
   __shared__ double sh[32];
   __shared__ bool last;
   if (st->converged) return;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * TZ;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * zc;
+  const int kend = min(F.nz, k0 + zc);
   const int tid = threadIdx.x, tx = tid & (TX - 1), ty = tid / TX;
   const T* rcur = level_r(F, st->iter);
-  {
-    const PlaneMap m = plane_map<H2X, H2Y>();
-#pragma unroll 2
-    for (int ez = 0; ez < H2Z; ++ez) {
-      const int gk = k0 - 2 + ez;
+  const size_t PS = (size_t)F.P * F.ny, PSC = (size_t)C.P * C.ny;
+  const PlaneMap mq = plane_map<QX, QY>();
+  const PlaneMap mx = plane_map<XX, XY>();
+  PosXY<T> pt[2], pu[2];
+  int st_[2], su[2], sut[2], par[2], poff[2];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (h == 1 && !m.has1) break;
-        const int ex = h ? m.x1 : m.x0, ey = h ? m.y1 : m.y0;
-        const int hi = i0 - 2 + ex, hj = j0 - 2 + ey;
-        T v = 0;
-        if (in_level(F, hi, hj, gk)) {
-          const int pi = F.cx ? hi >> 1 : hi, pj = F.cy ? hj >> 1 : hj, pk = F.cz ? gk >> 1 : gk;
-          v = F.x[lidx(F, hi, hj, gk)] + C.t[lidx(C, pi, pj, pk)];
-        }
-        St[ex + H2X * ey + H2P * ez] = v;
-      }
-    }
+  for (int h = 0; h < 2; ++h) {
+    const int qx = h ? mq.x1 : mq.x0, qy = h ? mq.y1 : mq.y0;
+    const int hi = i0 - 2 + qx, hj = j0 - 2 + qy;
+    pt[h] = pos_xy(F, hi, hj);
+    if (h == 1 && !mq.has1) pt[h].ok = false;
+    st_[h] = qx + QX * qy;
+    poff[h] = pt[h].ok ? (F.cx ? hi >> 1 : hi) + C.P * (F.cy ? hj >> 1 : hj) : 0;
+    const int xx = h ? mx.x1 : mx.x0, xy = h ? mx.y1 : mx.y0;
+    pu[h] = pos_xy(F, i0 - 1 + xx, j0 - 1 + xy);
+    if (h == 1 && !mx.has1) pu[h].ok = false;
+    su[h] = xx + XX * xy;
+    sut[h] = (xx + 1) + QX * (xy + 1);
+    par[h] = (i0 - 1 + xx + j0 - 1 + xy) & 1;
   }
-  __syncthreads();
-  // first pass over tile + halo 1 (Jacobi sweep / black cells)
-  {
-    const PlaneMap m = plane_map<H1X, H1Y>();
-#pragma unroll 2
-    for (int ez = 0; ez < H1Z; ++ez) {
-      const int gk = k0 - 1 + ez;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (h == 1 && !m.has1) break;
-        const int ex = h ? m.x1 : m.x0, ey = h ? m.y1 : m.y0;
-        const int hi = i0 - 1 + ex, hj = j0 - 1 + ey;
-        T v = 0;
-        if (in_level(F, hi, hj, gk)) {
-          const int b = (ex + 1) + H2X * (ey + 1) + H2P * (ez + 1);
-          v = relax<SM>(St[b], rcur[lidx(F, hi, hj, gk)], nbs<T, H2X, H2P>(F, St, b), diag_of(F, hi, hj, gk), omega,
-                        ((hi + hj + gk) & 1) == 1);
-        }
-        Su[ex + H1X * ey + H1P * ez] = v;
-      }
-    }
-  }
-  __syncthreads();
   const int gi = i0 + tx, gj = j0 + ty;
-  double acc = 0.0;
-  if (gi < F.nx && gj < F.ny) {
+  const PosXY<T> po = pos_xy(F, gi, gj);
+  const int opar = (gi + gj) & 1;
+  T px[2], pe[2];   // t-plane loads in flight
+  T pr[2];          // r on the halo-1 plane in flight
+  auto issueT = [&](int k) {
+    const bool kin = (unsigned)k < (unsigned)F.nz;
+    const int pk = F.cz ? k >> 1 : k;
 #pragma unroll
-    for (int z = 0; z < TZ; ++z) {
-      const int gk = k0 + z;
-      if (gk >= F.nz) break;
-      const int b = (tx + 1) + H1X * (ty + 1) + H1P * (z + 1);
-      const size_t c = lidx(F, gi, gj, gk);
-      const T rc = rcur[c];
-      const T zv = relax<SM>(Su[b], rc, nbs<T, H1X, H1P>(F, Su, b), diag_of(F, gi, gj, gk), omega,
-                             ((gi + gj + gk) & 1) == 0);
-      out[c] = zv;
-      if (FINEST) acc += (double)rc * (double)zv;
+    for (int h = 0; h < 2; ++h) {
+      px[h] = 0;
+      pe[h] = 0;
+      if (kin && pt[h].ok) {
+        px[h] = F.x[(size_t)k * PS + pt[h].off];
+        pe[h] = C.t[(size_t)pk * PSC + poff[h]];
+      }
+    }
+  };
+  auto commitT = [&](int k) {
+    T* dst = sT[ring4(k)];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && !mq.has1) break;
+      dst[st_[h]] = px[h] + pe[h];
+    }
+  };
+  auto issueR = [&](int k) {
+    const bool kin = (unsigned)k < (unsigned)F.nz;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) pr[h] = (kin && pu[h].ok) ? rcur[(size_t)k * PS + pu[h].off] : T(0);
+  };
+  auto computeU = [&](int k) {
+    T* dst = sU[ring3(k)];
+    const T* tm = sT[ring4(k - 1)];
+    const T* tc = sT[ring4(k)];
+    const T* tp = sT[ring4(k + 1)];
+    const bool kin = (unsigned)k < (unsigned)F.nz;
+    const T dz = diag_z(F, k);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && !mx.has1) break;
+      T v = 0;
+      if (kin && pu[h].ok) {
+        const int b = sut[h];
+        const T s = F.wx * (tc[b - 1] + tc[b + 1]) + F.wy * (tc[b - QX] + tc[b + QX]) + F.wz * (tm[b] + tp[b]);
+        v = relax<SM>(tc[b], pr[h], s, pu[h].dxy + dz, omega, ((par[h] + k) & 1) == 1);
+      }
+      dst[su[h]] = v;
+    }
+  };
+  double acc = 0.0;
+  DotAcc<T> dacc;
+  issueT(k0 - 2); commitT(k0 - 2);
+  issueT(k0 - 1); commitT(k0 - 1);
+  issueT(k0); commitT(k0);
+  issueT(k0 + 1);
+  issueR(k0 - 1);
+  __syncthreads();
+  computeU(k0 - 1);
+  commitT(k0 + 1);
+  issueT(k0 + 2);
+  issueR(k0);
+  __syncthreads();
+  computeU(k0);
+  issueR(k0 + 1);
+  __syncthreads();
+  const int b = (tx + 1) + XX * (ty + 1);
+  for (int k = k0; k < kend; ++k) {
+    T o_r = 0;
+    const size_t oc = (size_t)k * PS + po.off;
+    if (po.ok) o_r = rcur[oc];
+    commitT(k + 2);
+    issueT(k + 3);
+    __syncthreads();
+    computeU(k + 1);
+    issueR(k + 2);
+    __syncthreads();
+    if (po.ok) {
+      const T* um = sU[ring3(k - 1)];
+      const T* uc = sU[ring3(k)];
+      const T* up = sU[ring3(k + 1)];
+      const T s = F.wx * (uc[b - 1] + uc[b + 1]) + F.wy * (uc[b - XX] + uc[b + XX]) + F.wz * (um[b] + up[b]);
+      const T zv = relax<SM>(uc[b], o_r, s, po.dxy + diag_z(F, k), omega, ((opar + k) & 1) == 0);
+      out[oc] = zv;
+      if (FINEST) dacc.add(o_r, zv);
     }
   }
   if (FINEST) {
+    acc += dacc.value();
     acc = block_sum<FT>(acc, sh);
     const double vals[1] = {acc};
     if (publish_partials<1>(partials, &st->ticket[0], vals, &last)) {
@@ -486,59 +634,81 @@ __global__ void __launch_bounds__(TAIL_T) k_mg_tail(TailArgs<T> A, T omega, cons
 }
 
 // ------------------------------------------- CG direction + SpMV --------
-// d = z (first iteration) or z + beta d_old over tile + halo 1 in shared
-// memory; q = A d on the owned cells; d.q and alpha = rz / d.q.
+// d = z (first iteration) or z + beta d_old, staged per z plane on the tile
+// plus a halo of 1 (ring of 4 planes, one barrier per plane, loads one plane
+// ahead); q = A d on the owned cells; d.q and alpha = rz / d.q.
 template <typename T>
-__global__ void __launch_bounds__(FT) k_cg_dir_q(Level<T> L, const T* __restrict__ z, T* d0, T* d1,
+__global__ void __launch_bounds__(FT) k_cg_dir_q(Level<T> L, int zc, const T* __restrict__ z, T* d0, T* d1,
                                                 T* __restrict__ q, double* partials, SolveState* st) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Sd = reinterpret_cast<T*>(smem_raw);   // H1N (0 outside)
+  __shared__ T sD[4][XP];
   __shared__ double sh[32];
   __shared__ bool last;
   if (st->converged) return;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * TZ;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * zc;
+  const int kend = min(L.nz, k0 + zc);
   const int tid = threadIdx.x, tx = tid & (TX - 1), ty = tid / TX;
   const int it = st->iter;
   const T* dold = (it & 1) ? d1 : d0;
   T* dnew = (it & 1) ? d0 : d1;
   const T beta = it == 0 ? T(0) : (T)st->beta;
-  {
-    const PlaneMap m = plane_map<H1X, H1Y>();
-#pragma unroll 2
-    for (int ez = 0; ez < H1Z; ++ez) {
-      const int gk = k0 - 1 + ez;
+  const size_t PS = (size_t)L.P * L.ny;
+  const PlaneMap mx = plane_map<XX, XY>();
+  PosXY<T> pd[2];
+  int sd[2];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (h == 1 && !m.has1) break;
-        const int ex = h ? m.x1 : m.x0, ey = h ? m.y1 : m.y0;
-        const int hi = i0 - 1 + ex, hj = j0 - 1 + ey;
-        T v = 0;
-        if (in_level(L, hi, hj, gk)) {
-          const size_t c = lidx(L, hi, hj, gk);
-          v = it == 0 ? z[c] : z[c] + beta * dold[c];
-        }
-        Sd[ex + H1X * ey + H1P * ez] = v;
+  for (int h = 0; h < 2; ++h) {
+    const int xx = h ? mx.x1 : mx.x0, xy = h ? mx.y1 : mx.y0;
+    pd[h] = pos_xy(L, i0 - 1 + xx, j0 - 1 + xy);
+    if (h == 1 && !mx.has1) pd[h].ok = false;
+    sd[h] = xx + XX * xy;
+  }
+  T pz[2], pdv[2];
+  auto issueD = [&](int k) {
+    const bool kin = (unsigned)k < (unsigned)L.nz;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      pz[h] = 0;
+      pdv[h] = 0;
+      if (kin && pd[h].ok) {
+        const size_t c = (size_t)k * PS + pd[h].off;
+        pz[h] = z[c];
+        if (it != 0) pdv[h] = dold[c];
       }
     }
-  }
-  __syncthreads();
-  const int gi = i0 + tx, gj = j0 + ty;
-  double acc = 0.0;
-  if (gi < L.nx && gj < L.ny) {
+  };
+  auto commitD = [&](int k) {
+    T* dst = sD[ring4(k)];
 #pragma unroll
-    for (int zz = 0; zz < TZ; ++zz) {
-      const int gk = k0 + zz;
-      if (gk >= L.nz) break;
-      const int b = (tx + 1) + H1X * (ty + 1) + H1P * (zz + 1);
-      const T dc = Sd[b];
-      const T qv = diag_of(L, gi, gj, gk) * dc - nbs<T, H1X, H1P>(L, Sd, b);
-      const size_t c = lidx(L, gi, gj, gk);
-      dnew[c] = dc;
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && !mx.has1) break;
+      dst[sd[h]] = pz[h] + beta * pdv[h];
+    }
+  };
+  const int gi = i0 + tx, gj = j0 + ty;
+  const PosXY<T> po = pos_xy(L, gi, gj);
+  const int b = (tx + 1) + XX * (ty + 1);
+  DotAcc<T> dacc;
+  issueD(k0 - 1); commitD(k0 - 1);
+  issueD(k0); commitD(k0);
+  issueD(k0 + 1);
+  for (int k = k0; k < kend; ++k) {
+    commitD(k + 1);
+    issueD(k + 2);
+    __syncthreads();
+    if (po.ok) {
+      const T* dm = sD[ring4(k - 1)];
+      const T* dc = sD[ring4(k)];
+      const T* dp = sD[ring4(k + 1)];
+      const T dv = dc[b];
+      const T qv = (po.dxy + diag_z(L, k)) * dv -
+                   (L.wx * (dc[b - 1] + dc[b + 1]) + L.wy * (dc[b - XX] + dc[b + XX]) + L.wz * (dm[b] + dp[b]));
+      const size_t c = (size_t)k * PS + po.off;
+      dnew[c] = dv;
       q[c] = qv;
-      acc += (double)dc * (double)qv;
+      dacc.add(dv, qv);
     }
   }
-  acc = block_sum<FT>(acc, sh);
+  double acc = block_sum<FT>(dacc.value(), sh);
   const double vals[1] = {acc};
   if (publish_partials<1>(partials, &st->ticket[2], vals, &last)) {
     double tot[1];

@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(NT) k_cg_init(Level<T> L, const T* __restrict_
   UF_CELL_LOOP(L);
   const bool zero_rhs = st->bb == 0.0;
   double acc = 0.0;
+  DotAcc<T> dacc;
   if (inside) {
     for (int k = z0; k < z1; ++k) {
       const size_t c = lidx(L, i, j, k);
@@ -106,10 +107,11 @@ __global__ void __launch_bounds__(NT) k_cg_init(Level<T> L, const T* __restrict_
         const T ax = level_apply(L, i, j, k, [&](int a, int b2, int c2) { return x[lidx(L, a, b2, c2)]; });
         const T rv = b[c] - ax;
         L.r[c] = rv;
-        acc += (double)rv * (double)rv;
+        dacc.add(rv, rv);
       }
     }
   }
+  acc += dacc.value();
   acc = block_sum<NT>(acc, sh);
   const double vals[1] = {acc};
   if (publish_partials<1>(partials, &st->ticket[1], vals, &last)) {
@@ -147,6 +149,7 @@ __global__ void __launch_bounds__(NT) k_cg_direction_spmv(Level<T> L, const T* _
     return first ? z[c] : z[c] + beta * dold[c];
   };
   double acc = 0.0;
+  DotAcc<T> dacc;
   if (inside) {
     for (int k = z0; k < z1; ++k) {
       const size_t c = lidx(L, i, j, k);
@@ -154,9 +157,10 @@ __global__ void __launch_bounds__(NT) k_cg_direction_spmv(Level<T> L, const T* _
       const T qv = level_apply(L, i, j, k, dn);
       dnew[c] = dc;
       q[c] = qv;
-      acc += (double)dc * (double)qv;
+      dacc.add(dc, qv);
     }
   }
+  acc += dacc.value();
   acc = block_sum<NT>(acc, sh);
   const double vals[1] = {acc};
   if (publish_partials<1>(partials, &st->ticket[2], vals, &last)) {
@@ -183,15 +187,17 @@ __global__ void __launch_bounds__(NT) k_cg_update(Level<T> L, T* __restrict__ x,
   const T* d = (it & 1) ? d0 : d1;
   const T alpha = (T)st->alpha;
   double acc = 0.0;
+  DotAcc<T> dacc;
   if (inside) {
     for (int k = z0; k < z1; ++k) {
       const size_t c = lidx(L, i, j, k);
       x[c] += alpha * d[c];
       const T rv = L.r[c] - alpha * q[c];
       L.r[c] = rv;
-      acc += (double)rv * (double)rv;
+      dacc.add(rv, rv);
     }
   }
+  acc += dacc.value();
   acc = block_sum<NT>(acc, sh);
   const double vals[1] = {acc};
   if (publish_partials<1>(partials, &st->ticket[3], vals, &last)) {
@@ -268,6 +274,7 @@ __global__ void __launch_bounds__(NT) k_precond_simple(Level<T> L, int kind, T w
   if (st->converged) return;
   UF_CELL_LOOP(L);
   double acc = 0.0;
+  DotAcc<T> dacc;
   if (inside) {
     for (int k = z0; k < z1; ++k) {
       const size_t c = lidx(L, i, j, k);
@@ -281,9 +288,10 @@ __global__ void __launch_bounds__(NT) k_precond_simple(Level<T> L, int kind, T w
         zv = ai1_apply(L, L.r, w, i, j, k);
       }
       z[c] = zv;
-      acc += (double)L.r[c] * (double)zv;
+      dacc.add(L.r[c], zv);
     }
   }
+  acc += dacc.value();
   acc = block_sum<NT>(acc, sh);
   const double vals[1] = {acc};
   if (publish_partials<1>(partials, &st->ticket[0], vals, &last)) {
@@ -312,13 +320,13 @@ __global__ void __launch_bounds__(NT) k_solve_reset(Level<T> L, const T* __restr
   __shared__ double sh[32];
   __shared__ bool last;
   UF_CELL_LOOP(L);
-  double acc = 0.0;
+  DotAcc<T> dacc;
   if (inside)
     for (int k = z0; k < z1; ++k) {
-      const double bv = (double)b[lidx(L, i, j, k)];
-      acc += bv * bv;
+      const T bv = b[lidx(L, i, j, k)];
+      dacc.add(bv, bv);
     }
-  acc = block_sum<NT>(acc, sh);
+  double acc = block_sum<NT>(dacc.value(), sh);
   const double vals[1] = {acc};
   if (publish_partials<1>(partials, &st->ticket[0], vals, &last)) {
     double tot[1];

@@ -19,21 +19,25 @@ constexpr int BX = 32, BY = 8, NT = BX * BY;
 template <typename T>
 __global__ void __launch_bounds__(256) k_cfl_dt(const T* __restrict__ u, size_t nu, const T* __restrict__ v,
                                                 size_t nv, const T* __restrict__ w, size_t nw, double cfl_h,
-                                                double* partials, unsigned int* ticket, double* dt_out) {
+                                                double* partials, unsigned int* ticket, double* dt_out,
+                                                T* dtT_out) {
   __shared__ double sh[32];
   __shared__ bool last;
-  double m = 0.0;
+  T mt = 0;   // max in the field type (exact), one conversion per thread
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  for (size_t q = t0; q < nu; q += stride) m = fmax(m, (double)fabs(u[q]));
-  for (size_t q = t0; q < nv; q += stride) m = fmax(m, (double)fabs(v[q]));
-  for (size_t q = t0; q < nw; q += stride) m = fmax(m, (double)fabs(w[q]));
-  m = block_max<256>(m, sh);
+  for (size_t q = t0; q < nu; q += stride) mt = fmax(mt, fabs(u[q]));
+  for (size_t q = t0; q < nv; q += stride) mt = fmax(mt, fabs(v[q]));
+  for (size_t q = t0; q < nw; q += stride) mt = fmax(mt, fabs(w[q]));
+  double m = block_max<256>((double)mt, sh);
   const double vals[1] = {m};
   if (publish_partials<1>(partials, ticket, vals, &last)) {
     const double mx = reduce_partials_max<256>(partials, sh);
     if (threadIdx.x == 0) {
-      if (mx > 0.0) *dt_out = cfl_h / mx;
+      if (mx > 0.0) {
+        *dt_out = cfl_h / mx;
+        *dtT_out = (T)(cfl_h / mx);
+      }
       *ticket = 0u;
     }
   }
@@ -87,7 +91,7 @@ __global__ void __launch_bounds__(NT) k_eddy_viscosity(StepParams<T> p, const T*
                                                        T* __restrict__ nut) {
   const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= p.nx || j >= p.ny) return;
-  const T dt = (T)*p.dt;
+  const T dt = *p.dtT;
   const size_t c = idx_c(p, i, j, k);
   nut[c] = limited_nut(p, kf[c], om[c], strain_sq(u, v, w, p, i, j, k), dt);
 }
@@ -148,7 +152,7 @@ struct AdvectArgs {
   T* wt;              // MacCormack result (interior faces only)
   Lattice Lu, Lv, Lw;
   int nx, ny, nz;
-  const double* dt;
+  const T* dtT;
   T inv_h;
 };
 
@@ -186,7 +190,7 @@ __global__ void __launch_bounds__(NT) k_advect_forward(AdvectArgs<T> A) {
   const Lattice L = q == 0 ? A.Lu : (q == 1 ? A.Lv : A.Lw);
   const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   if (i >= L.Lx || j >= L.Ly) return;
-  const T s = (T)(*A.dt) * A.inv_h;
+  const T s = *A.dtT * A.inv_h;
   const T* F = q == 0 ? A.u : (q == 1 ? A.v : A.w);
   T* Fh = q == 0 ? A.uh : (q == 1 ? A.vh : A.wh);
   T d[3];
@@ -207,7 +211,7 @@ __global__ void __launch_bounds__(NT) k_advect_backward(AdvectArgs<T> A) {
   if (i >= L.Lx || j >= L.Ly) return;
   const bool interior = q == 0 ? (i > 0 && i < A.nx) : (q == 1 ? (j > 0 && j < A.ny) : (k > 0 && k < A.nz));
   if (!interior) return;
-  const T s = (T)(*A.dt) * A.inv_h;
+  const T s = *A.dtT * A.inv_h;
   const T* F = q == 0 ? A.u : (q == 1 ? A.v : A.w);
   const T* Fh = q == 0 ? A.uh : (q == 1 ? A.vh : A.wh);
   T* Ft = q == 0 ? A.ut : (q == 1 ? A.vt : A.wt);
@@ -232,7 +236,7 @@ __global__ void __launch_bounds__(NT) k_diffuse(StepParams<T> p, const T* __rest
   int q, k;
   plane_of(blockIdx.z, p.nz, q, k);
   const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-  const T dt = (T)*p.dt;
+  const T dt = *p.dtT;
   const T c = dt * p.inv_h * p.inv_h;
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   if (q == 0) {
@@ -323,7 +327,7 @@ __global__ void __launch_bounds__(NT) k_drag_bc(StepParams<T> p, const T* __rest
   int q, k;
   plane_of(blockIdx.z, p.nz, q, k);
   const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-  const T dt = (T)*p.dt;
+  const T dt = *p.dtT;
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   if (q == 0) {
     if (i > nx || j >= ny) return;
@@ -372,14 +376,16 @@ __global__ void __launch_bounds__(NT) k_pressure_rhs(StepParams<T> p, const T* _
   const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   const int z0 = blockIdx.z * zc, z1 = min(p.nz, z0 + zc);
   double acc = 0.0;
+  DotAcc<T> dacc;
   if (i < p.nx && j < p.ny) {
-    const T sc = -p.rho * p.h / (T)*p.dt;
+    const T sc = -p.rho * p.h / *p.dtT;
     for (int k = z0; k < z1; ++k) {
       const T bv = sc * cell_flux(p, u, v, w, i, j, k);
       b[idx_c(p, i, j, k)] = bv;
-      acc += (double)bv * (double)bv;
+      dacc.add(bv, bv);
     }
   }
+  acc += dacc.value();
   acc = block_sum<NT>(acc, sh);
   const double vals[1] = {acc};
   if (publish_partials<1>(partials, &st->ticket[0], vals, &last)) {
@@ -404,7 +410,7 @@ __global__ void __launch_bounds__(NT) k_project(StepParams<T> p, const T* __rest
   int q, k;
   plane_of(blockIdx.z, p.nz, q, k);
   const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-  const T g = (T)*p.dt / (p.rho * p.h);
+  const T g = *p.dtT / (p.rho * p.h);
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   if (q == 0) {
     if (i > nx || j >= ny) return;
@@ -439,7 +445,7 @@ __global__ void __launch_bounds__(NT) k_turbulence(StepParams<T> p, const T* __r
                                                    const T* __restrict__ oi, T* __restrict__ ko, T* __restrict__ oo) {
   const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= p.nx || j >= p.ny) return;
-  const T dt = (T)*p.dt;
+  const T dt = *p.dtT;
   const size_t c = idx_c(p, i, j, k);
   const T kc = ki[c], oc = oi[c];
   const T S2 = strain_sq(u, v, w, p, i, j, k);

@@ -37,7 +37,8 @@ struct StepParams {
   T C_mu, alpha, beta, sigma, sigma_star, C_lim;
   T k_min, om_min, k_in, om_in;
   const T* prof;           // inflow speed at the nz cell-centre heights
-  const double* dt;        // device scalar: the step's time step
+  const double* dt;        // device scalar: the step's time step (FP64)
+  const T* dtT;            // the same time step in the field type (read per cell)
 };
 
 // ------------------------------------------------------------- indexing --
@@ -83,6 +84,37 @@ __device__ __forceinline__ T w_face(const T* __restrict__ w, const StepParams<T>
   if (k == 0 || k == p.nz) return T(0);
   return w[idx_c(p, i, j, k)];
 }
+
+// ----------------------------------------------------- dot accumulation --
+// Per-thread accumulator of sums of products.  For FP32 fields it is the
+// compensated "Dot2" scheme of Ogita, Rump and Oishi (SIAM J. Sci. Comput.
+// 26(6), 2005): every product is split exactly into p + e with an FMA, the
+// running sum is kept as an unevaluated pair (hi, lo) with Knuth's TwoSum,
+// so the result is as accurate as a sum accumulated in twice the working
+// precision -- while every operation stays on the FP32 pipes (GB300 issues
+// FP64 at 1/64 of the FP32 rate).  The pair is converted to FP64 once per
+// thread; block and grid sums are FP64.  For FP64 fields it is a plain
+// double sum.
+template <typename T>
+struct DotAcc {
+  double s = 0.0;
+  __device__ __forceinline__ void add(T a, T b) { s = fma((double)a, (double)b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);   // a*b = p + pe exactly
+    const float t = hi + p;            // TwoSum(hi, p) = t + te exactly
+    const float bv = t - hi;
+    const float te = (hi - (t - bv)) + (p - bv);
+    hi = t;
+    lo += te + pe;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 
 // ------------------------------------------------------------- reduction --
 // Deterministic block + grid reduction in FP64: every block writes one
