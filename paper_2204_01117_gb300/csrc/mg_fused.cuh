@@ -637,6 +637,12 @@ __global__ void __launch_bounds__(TAIL_T) k_mg_tail(TailArgs<T> A, T omega, cons
 // d = z (first iteration) or z + beta d_old, staged per z plane on the tile
 // plus a halo of 1 (ring of 4 planes, one barrier per plane, loads one plane
 // ahead); q = A d on the owned cells; d.q and alpha = rz / d.q.
+// q is formed as a sum of differences w (d_c - d_nb): the CG directions turn
+// smooth as the iteration proceeds, and the form D d_c - sum w d_nb would then
+// lose about eps * |D d| to cancellation in FP32 -- an error the recursive
+// residual never sees, which caps the attainable accuracy of the pressure.
+// A Neumann neighbour takes d_c (its term is exactly zero); an outlet
+// neighbour is the staged zero ghost (term w d_c).
 template <typename T>
 __global__ void __launch_bounds__(FT) k_cg_dir_q(Level<T> L, int zc, const T* __restrict__ z, T* d0, T* d1,
                                                 T* __restrict__ q, double* partials, SolveState* st) {
@@ -687,6 +693,8 @@ __global__ void __launch_bounds__(FT) k_cg_dir_q(Level<T> L, int zc, const T* __
   const int gi = i0 + tx, gj = j0 + ty;
   const PosXY<T> po = pos_xy(L, gi, gj);
   const int b = (tx + 1) + XX * (ty + 1);
+  const bool nxm = gi == 0 && !(L.out_mask & 1), nxp = gi == L.nx - 1 && !(L.out_mask & 2);
+  const bool nym = gj == 0 && !(L.out_mask & 4), nyp = gj == L.ny - 1 && !(L.out_mask & 8);
   DotAcc<T> dacc;
   issueD(k0 - 1); commitD(k0 - 1);
   issueD(k0); commitD(k0);
@@ -700,8 +708,11 @@ __global__ void __launch_bounds__(FT) k_cg_dir_q(Level<T> L, int zc, const T* __
       const T* dc = sD[ring4(k)];
       const T* dp = sD[ring4(k + 1)];
       const T dv = dc[b];
-      const T qv = (po.dxy + diag_z(L, k)) * dv -
-                   (L.wx * (dc[b - 1] + dc[b + 1]) + L.wy * (dc[b - XX] + dc[b + XX]) + L.wz * (dm[b] + dp[b]));
+      const T xm = nxm ? dv : dc[b - 1], xp = nxp ? dv : dc[b + 1];
+      const T ym = nym ? dv : dc[b - XX], yp = nyp ? dv : dc[b + XX];
+      const T zm = (k == 0 && !(L.out_mask & 16)) ? dv : dm[b];
+      const T zp = (k == L.nz - 1 && !(L.out_mask & 32)) ? dv : dp[b];
+      const T qv = L.wx * ((dv - xm) + (dv - xp)) + L.wy * ((dv - ym) + (dv - yp)) + L.wz * ((dv - zm) + (dv - zp));
       const size_t c = (size_t)k * PS + po.off;
       dnew[c] = dv;
       q[c] = qv;
