@@ -206,6 +206,52 @@ int uf_last_step_launches(uf_grid* g);
  * Builds the step graphs if needed. */
 uf_status uf_launch_counts(uf_grid* g, int* fixed, int* per_iter);
 
+/* ---- Discrete adjoint and design gradients ----------------------------
+ * The paper obtains design gradients by forward differences, N+1 forward
+ * simulations per gradient (Sec. 5, "Gradient-descent"; Sec. 6.2); these
+ * entry points give the same gradient from one forward and one reverse
+ * sweep: the hand-written transpose of every sub-step of uf_step (a1-a9 in
+ * reverse; the pressure solve is self-adjoint because A is symmetric) and of
+ * the comfort objective of uf_objective, with checkpointing every
+ * ckpt_every steps and recomputation of each segment.  Non-smooth points
+ * (clamps, limiters, upwind side, the drag cut-off, the MacCormack clamp)
+ * take the branch of the forward pass.  The initial state is held fixed. */
+
+/* Bytes of the caller-allocated device workspace uf_adjoint_run needs for
+ * nsteps steps with checkpoints every ckpt_every steps (0 on bad input):
+ * one taped segment of ckpt_every steps, the checkpoints and the adjoint
+ * fields. */
+size_t uf_adjoint_workspace_bytes(uf_grid* g, int nsteps, int ckpt_every);
+
+/* From the grid's current state X0, runs nsteps steps (the grid needs
+ * fixed_dt > 0), evaluates J = uf_objective(z_lo, z_hi, u_hi, u_lo) on the
+ * final state, and sweeps back to give dJ/dphi, the gradient with respect
+ * to the porosity field last set (dense cell field, grid precision, host or
+ * device pointer; may be NULL).  Afterwards the grid holds the final state,
+ * as after uf_run.  d_ws: device workspace of uf_adjoint_workspace_bytes().
+ * Synchronises.  Errors: UF_ERR_ARG (no fixed dt, bad sizes), UF_ERR_NOMEM,
+ * UF_ERR_STATE, and the solver errors of uf_step. */
+uf_status uf_adjoint_run(uf_grid* g, void* d_ws, size_t bytes, int nsteps, int ckpt_every, double z_lo, double z_hi,
+                         double u_hi, double u_lo, void* dJ_dphi, double* J_out);
+
+/* Parametric design -> porosity (smoothed cut-cell idea of Sec. 3, "Urban
+ * model resolving"): nbox (<= 64) boxes with base footprints
+ * boxes[4i..4i+3] = (x_a, x_b, y_a, y_b) [m] and parameters
+ * theta[3i..3i+2] = (height, x shift, y shift) [m];
+ * phi = prod_i (1 - chi_i), chi_i = s((x - x_a - dx)/w) s((x_b + dx - x)/w)
+ * s((y - y_a - dy)/w) s((y_b + dy - y)/w) s((H - z)/w) at cell centres, s the
+ * logistic function, w = width [m].  phi_out == NULL: sets the grid's
+ * porosity (as uf_set_porosity); else writes the dense field there (host or
+ * device).  boxes and theta are host arrays. */
+uf_status uf_design_to_phi(uf_grid* g, int nbox, const double* boxes, const double* theta, double width,
+                           void* phi_out);
+
+/* Vector-Jacobian product of uf_design_to_phi: dJ/dtheta (host, 3*nbox
+ * doubles) from dJ/dphi (dense cell field, grid precision, host or device).
+ * Synchronises. */
+uf_status uf_design_vjp(uf_grid* g, int nbox, const double* boxes, const double* theta, double width,
+                        const void* dJ_dphi, double* dJ_dtheta);
+
 /* ---- Pressure solve without any device allocation ---------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot call cudaMalloc or hand the library a workspace: code running

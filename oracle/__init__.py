@@ -270,3 +270,22 @@ class Oracle:
         st = OrcStats()
         self.lib.orc_run(self._h, nsteps, ctypes.byref(st))
         return st
+
+
+def design_to_phi(nx: int, ny: int, nz: int, h: float, boxes, theta, width: float) -> np.ndarray:
+    """Porosity of the parametric design, in FP64 numpy: the product over
+    boxes of (1 - chi), chi the product of five logistic ramps at the cell
+    centre -- across the two x faces and the two y faces of the shifted box
+    footprint and below its height (the smoothed cut-cell idea of Sec. 3,
+    "Urban model resolving")."""
+    boxes = np.asarray(boxes, dtype=np.float64).reshape(-1, 4)
+    theta = np.asarray(theta, dtype=np.float64).reshape(-1, 3)
+    z, y, x = np.meshgrid((np.arange(nz) + 0.5) * h, (np.arange(ny) + 0.5) * h, (np.arange(nx) + 0.5) * h,
+                          indexing="ij")
+    s = lambda t: 1.0 / (1.0 + np.exp(-t))
+    phi = np.ones((nz, ny, nx))
+    for (xa, xb, ya, yb), (H, dx, dy) in zip(boxes, theta):
+        chi = (s((x - (xa + dx)) / width) * s(((xb + dx) - x) / width) * s((y - (ya + dy)) / width)
+               * s(((yb + dy) - y) / width) * s((H - z) / width))
+        phi *= 1.0 - chi
+    return phi

@@ -18,6 +18,7 @@
 
 #include "../../include/uf.h"
 #include "mg_fused.cuh"
+#include "adjoint_kernels.cuh"
 
 namespace {
 
@@ -108,12 +109,12 @@ struct Plan {
   std::vector<LevelDims> levels;
   int coarse_n;
   // offsets
-  size_t u, v, w, uh, vh, wh, ut, vt, wt, k0, k1, o0, o1, cc, phi, nut, p, b, r, r2, z, q, d0, d1;
+  size_t u, v, w, uh, vh, wh, ut, vt, wt, u2, v2, w2, k0, k1, o0, o1, cc, phi, nut, p, b, r, r2, z, q, d0, d1;
   int tail_level;          // first level run by the shared-memory tail kernel
   size_t tail_smem;        // its dynamic shared memory (bytes)
   std::vector<int> tail_off;
   std::vector<size_t> lr, lx, lt;
-  size_t prof, dt, dtT, scal, state, partials, ainv;
+  size_t prof, dt, dtT, scal, state, partials, ainv, boxes, grad;
   size_t total;
 };
 
@@ -132,6 +133,7 @@ Plan make_plan(const uf_grid_desc* d) {
   P.u = L.take(P.n_u * tb); P.v = L.take(P.n_v * tb); P.w = L.take(P.n_w * tb);
   P.uh = L.take(P.n_u * tb); P.vh = L.take(P.n_v * tb); P.wh = L.take(P.n_w * tb);
   P.ut = L.take(P.n_u * tb); P.vt = L.take(P.n_v * tb); P.wt = L.take(P.n_w * tb);
+  P.u2 = L.take(P.n_u * tb); P.v2 = L.take(P.n_v * tb); P.w2 = L.take(P.n_w * tb);
   P.k0 = L.take(P.n_c * tb); P.k1 = L.take(P.n_c * tb);
   P.o0 = L.take(P.n_c * tb); P.o1 = L.take(P.n_c * tb);
   P.cc = L.take(P.n_c * tb); P.phi = L.take(P.n_c * tb); P.nut = L.take(P.n_c * tb);
@@ -182,6 +184,8 @@ Plan make_plan(const uf_grid_desc* d) {
   P.state = L.take(sizeof(uf::SolveState));
   P.partials = L.take(sizeof(double) * kPartials * 2);
   P.ainv = L.take(sizeof(double) * (size_t)P.coarse_n * P.coarse_n);
+  P.boxes = L.take(sizeof(uf::DesignBox) * uf::MAX_BOXES);
+  P.grad = L.take(sizeof(double) * 3 * uf::MAX_BOXES);
   P.total = L.off + 256;
   return P;
 }
@@ -282,6 +286,10 @@ struct uf_grid {
   virtual int last_launches() = 0;
   virtual uf_status launch_counts(int*, int*) = 0;
   virtual uf_status profile_step(uf_kernel_time*, int, int*, uf_step_stats*) = 0;
+  virtual size_t adjoint_bytes(int, int) = 0;
+  virtual uf_status adjoint_run(void*, size_t, int, int, double, double, double, double, void*, double*) = 0;
+  virtual uf_status design_phi(int, const double*, const double*, double, void*) = 0;
+  virtual uf_status design_vjp(int, const double*, const double*, double, const void*, double*) = 0;
 };
 
 namespace {
@@ -295,8 +303,10 @@ class GridImpl final : public uf_grid {
   cudaStream_t stream = nullptr, cap = nullptr, cap2 = nullptr;
   uf::StepParams<T> sp;
   std::vector<uf::Level<T>> lv;
-  T *u, *v, *w, *uh, *vh, *wh, *ut, *vt, *wt, *kb[2], *ob[2], *cc, *phi, *nut, *p, *b, *r, *r2, *z, *q, *d0, *d1, *prof;
+  T *u, *v, *w, *uh, *vh, *wh, *ut, *vt, *wt, *u2, *v2, *w2, *kb[2], *ob[2], *cc, *phi, *nut, *p, *b, *r, *r2, *z, *q, *d0, *d1, *prof;
   uf::TailArgs<T> tail;
+  T* sol_x = nullptr;   // the solve's unknown (p for the step; mu for the adjoint)
+  T* sol_b = nullptr;   // its right-hand side
   double *dt, *scal, *partials, *ainv;
   T* dtT;
   uf::SolveState* st;
@@ -311,6 +321,7 @@ class GridImpl final : public uf_grid {
     for (auto& e : pool) cudaEventDestroy(e);
     if (init_exec) cudaGraphExecDestroy(init_exec);
     if (solve_exec) cudaGraphExecDestroy(solve_exec);
+    if (adj_solve_exec) cudaGraphExecDestroy(adj_solve_exec);
     if (cap) cudaStreamDestroy(cap);
     if (cap2) cudaStreamDestroy(cap2);
   }
@@ -328,8 +339,11 @@ class GridImpl final : public uf_grid {
     u = at<T>(P.u); v = at<T>(P.v); w = at<T>(P.w);
     uh = at<T>(P.uh); vh = at<T>(P.vh); wh = at<T>(P.wh);
     ut = at<T>(P.ut); vt = at<T>(P.vt); wt = at<T>(P.wt);
+    u2 = at<T>(P.u2); v2 = at<T>(P.v2); w2 = at<T>(P.w2);
     kb[0] = at<T>(P.k0); kb[1] = at<T>(P.k1); ob[0] = at<T>(P.o0); ob[1] = at<T>(P.o1);
     cc = at<T>(P.cc); phi = at<T>(P.phi); nut = at<T>(P.nut); p = at<T>(P.p); b = at<T>(P.b);
+    sol_x = p;
+    sol_b = b;
     r = at<T>(P.r); r2 = at<T>(P.r2); z = at<T>(P.z); q = at<T>(P.q); d0 = at<T>(P.d0); d1 = at<T>(P.d1);
     prof = at<T>(P.prof);
     dt = at<double>(P.dt); dtT = at<T>(P.dtT); scal = at<double>(P.scal); partials = at<double>(P.partials);
@@ -496,7 +510,7 @@ class GridImpl final : public uf_grid {
       const dim3 g = march_grid(lv[l], &zc);
       if (l == 0 && mode == 1)
         L(s, "mg_down_cg_L0", (7 * Nl(0) + Nl(1)) * tb(), [&] {
-          uf::k_mg_down<T, SM, true><<<g, uf::FT, 0, s>>>(lv[0], lv[1], om, zc, p, d0, d1, q, partials, st, cond,
+          uf::k_mg_down<T, SM, true><<<g, uf::FT, 0, s>>>(lv[0], lv[1], om, zc, sol_x, d0, d1, q, partials, st, cond,
                                                          use_cond);
         });
       else
@@ -545,7 +559,7 @@ class GridImpl final : public uf_grid {
     int zc;
     dim3 g = chunk_grid(lv[0].nx, lv[0].ny, lv[0].nz, &zc);
     L(s, "cg_init", 3 * N() * tb(), [&] {
-      uf::k_cg_init<T><<<g, dim3(uf::BX, uf::BY), 0, s>>>(lv[0], b, p, zc, partials, st, cond, use_cond);
+      uf::k_cg_init<T><<<g, dim3(uf::BX, uf::BY), 0, s>>>(lv[0], sol_b, sol_x, zc, partials, st, cond, use_cond);
     });
   }
   void rec_cg_iter(cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
@@ -564,7 +578,7 @@ class GridImpl final : public uf_grid {
       uf::k_cg_direction_spmv<T><<<g, dim3(uf::BX, uf::BY), 0, s>>>(lv[0], z, d0, d1, q, zc, partials, st);
     });
     L(s, "cg_update", 6 * N() * tb(), [&] {
-      uf::k_cg_update<T><<<g, dim3(uf::BX, uf::BY), 0, s>>>(lv[0], p, d0, d1, q, zc, partials, st, cond, use_cond);
+      uf::k_cg_update<T><<<g, dim3(uf::BX, uf::BY), 0, s>>>(lv[0], sol_x, d0, d1, q, zc, partials, st, cond, use_cond);
     });
   }
 
@@ -642,8 +656,8 @@ class GridImpl final : public uf_grid {
     const dim3 ga = plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1);
     L(s, "advect_forward", 2 * faces, [&] { uf::k_advect_forward<T><<<ga, blk, 0, s>>>(A); });
     L(s, "advect_backward", 3 * faces, [&] { uf::k_advect_backward<T><<<ga, blk, 0, s>>>(A); });
-    L(s, "diffuse", 2 * faces + cells, [&] { uf::k_diffuse<T><<<ga, blk, 0, s>>>(sp, ut, vt, wt, nut, uh, vh, wh); });
-    L(s, "drag_bc", 2 * faces + cells, [&] { uf::k_drag_bc<T><<<ga, blk, 0, s>>>(sp, uh, vh, wh, cc, u, v, w); });
+    L(s, "diffuse", 2 * faces + cells, [&] { uf::k_diffuse<T><<<ga, blk, 0, s>>>(sp, ut, vt, wt, nut, u2, v2, w2); });
+    L(s, "drag_bc", 2 * faces + cells, [&] { uf::k_drag_bc<T><<<ga, blk, 0, s>>>(sp, u2, v2, w2, cc, u, v, w); });
     int zc;
     const dim3 gr = chunk_grid(d.nx, d.ny, d.nz, &zc);
     L(s, "pressure_rhs", faces + cells, [&] { uf::k_pressure_rhs<T><<<gr, blk, 0, s>>>(sp, u, v, w, b, zc, partials, st); });
@@ -697,6 +711,269 @@ class GridImpl final : public uf_grid {
     return check_device(stats);
   }
   int last_profile_launches = 0;
+
+  // ------------------------------------------------------------ adjoint ---
+  // Workspace of uf_adjoint_run (caller-allocated): per-step tapes of one
+  // checkpoint segment, the checkpoints, the final state and the adjoint
+  // arrays.  Offsets in elements of T, every array 64-element aligned.
+  struct AdjLayout {
+    size_t faceN, cellN, slot, ckpt, total;
+    int C, nseg;
+    size_t tape0, ckpt0, fin, lam;
+    // offsets inside one tape slot; a slot starts with a checkpoint
+    // (faces | k | omega | p) so that save_state() fills its head
+    size_t s_nut, s_uh, s_ut, s_u2, s_u1;
+  };
+  static size_t a64(size_t n) { return (n + 63) / 64 * 64; }
+  size_t face_set() const { return a64(P.n_u) + a64(P.n_v) + a64(P.n_w); }
+  AdjLayout adj_layout(int nsteps, int C) const {
+    AdjLayout A;
+    A.faceN = face_set();
+    A.cellN = a64(P.n_c);
+    A.C = C;
+    A.nseg = (nsteps + C - 1) / C;
+    A.ckpt = A.faceN + 3 * A.cellN;       // faces, k, omega, p
+    A.s_nut = A.ckpt;
+    A.s_uh = A.s_nut + A.cellN;
+    A.s_ut = A.s_uh + A.faceN;
+    A.s_u2 = A.s_ut + A.faceN;
+    A.s_u1 = A.s_u2 + A.faceN;
+    A.slot = A.s_u1 + A.faceN;
+    A.tape0 = 0;
+    A.ckpt0 = A.tape0 + (size_t)C * A.slot;
+    A.fin = A.ckpt0 + (size_t)A.nseg * A.ckpt;
+    A.lam = A.fin + A.ckpt;
+    A.total = A.lam + 5 * A.faceN + 9 * A.cellN;
+    return A;
+  }
+  size_t adjoint_bytes(int nsteps, int C) override {
+    if (nsteps < 1 || C < 1) return 0;
+    return adj_layout(nsteps, C).total * sizeof(T) + 256;
+  }
+  struct FaceSet {
+    T *u, *v, *w;
+  };
+  FaceSet faces_at(T* base) const {
+    FaceSet f;
+    f.u = base;
+    f.v = base + a64(P.n_u);
+    f.w = f.v + a64(P.n_v);
+    return f;
+  }
+  cudaError_t copy_faces(FaceSet dst, const T* su, const T* sv, const T* sw) {
+    cudaError_t e = cudaMemcpyAsync(dst.u, su, P.n_u * sizeof(T), cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst.v, sv, P.n_v * sizeof(T), cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst.w, sw, P.n_w * sizeof(T), cudaMemcpyDeviceToDevice, stream);
+    return e;
+  }
+  cudaError_t copy_cell(T* dst, const T* src) {
+    return cudaMemcpyAsync(dst, src, P.n_c * sizeof(T), cudaMemcpyDeviceToDevice, stream);
+  }
+  // checkpoint layout: faces | k | omega | p
+  cudaError_t save_state(T* slot, const AdjLayout& A) {
+    FaceSet f = faces_at(slot);
+    cudaError_t e = copy_faces(f, u, v, w);
+    if (e == cudaSuccess) e = copy_cell(slot + A.faceN, kb[parity]);
+    if (e == cudaSuccess) e = copy_cell(slot + A.faceN + A.cellN, ob[parity]);
+    if (e == cudaSuccess) e = copy_cell(slot + A.faceN + 2 * A.cellN, p);
+    return e;
+  }
+  cudaError_t load_state(const T* slot, const AdjLayout& A) {
+    parity = 0;
+    FaceSet f = faces_at(const_cast<T*>(slot));
+    cudaError_t e = cudaMemcpyAsync(u, f.u, P.n_u * sizeof(T), cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(v, f.v, P.n_v * sizeof(T), cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w, f.w, P.n_w * sizeof(T), cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess) e = copy_cell(kb[0], slot + A.faceN);
+    if (e == cudaSuccess) e = copy_cell(ob[0], slot + A.faceN + A.cellN);
+    if (e == cudaSuccess) e = copy_cell(p, slot + A.faceN + 2 * A.cellN);
+    return e;
+  }
+
+  cudaGraphExec_t adj_solve_exec = nullptr;
+  T* adj_mu = nullptr;
+  T* adj_b = nullptr;
+
+  uf_status adjoint_run(void* wsp, size_t bytes, int nsteps, int C, double z_lo, double z_hi, double u_hi, double u_lo,
+                        void* dJ_dphi, double* J_out) override {
+    if (!(d.fixed_dt > 0)) return fail(UF_ERR_ARG, "uf_adjoint_run needs a fixed time step (fixed_dt > 0)");
+    if (!have_state) return fail(UF_ERR_STATE, "no state: call uf_init_state or uf_set_state first");
+    if (!wsp || nsteps < 1 || C < 1) return fail(UF_ERR_ARG, "need a workspace, nsteps >= 1 and ckpt_every >= 1");
+    if (bytes < adjoint_bytes(nsteps, C)) return fail(UF_ERR_NOMEM, "adjoint workspace smaller than uf_adjoint_workspace_bytes()");
+    const AdjLayout A = adj_layout(nsteps, C);
+    T* base = reinterpret_cast<T*>(round_up(reinterpret_cast<size_t>(wsp), 256));
+    uf_status s = build_step_graphs();
+    if (s != UF_OK) return s;
+    // adjoint arrays
+    T* lam = base + A.lam;
+    FaceSet L0 = faces_at(lam), L1 = faces_at(lam + A.faceN), Lt = faces_at(lam + 2 * A.faceN),
+            L2 = faces_at(lam + 3 * A.faceN), Lh = faces_at(lam + 4 * A.faceN);
+    T* cells = lam + 5 * A.faceN;
+    T *lk0 = cells, *lk1 = cells + A.cellN, *lo0 = cells + 2 * A.cellN, *lo1 = cells + 3 * A.cellN;
+    T *lnut = cells + 4 * A.cellN, *lc = cells + 5 * A.cellN, *mu = cells + 6 * A.cellN, *badj = cells + 7 * A.cellN;
+    T* lphi = cells + 8 * A.cellN;
+    // the adjoint pressure solve: its own graph over (badj -> mu)
+    if (!adj_solve_exec || adj_mu != mu || adj_b != badj) {
+      if (adj_solve_exec) cudaGraphExecDestroy(adj_solve_exec);
+      adj_solve_exec = nullptr;
+      sol_x = mu;
+      sol_b = badj;
+      int nf, ns, ni;
+      auto pre = [&](cudaStream_t s2) {
+        int zc;
+        dim3 g = chunk_grid(d.nx, d.ny, d.nz, &zc);
+        uf::k_solve_reset<T><<<g, dim3(uf::BX, uf::BY), 0, s2>>>(lv[0], badj, zc, partials, st);
+        rec_count++;
+      };
+      s = capture(&adj_solve_exec, pre, [&](cudaStream_t) {}, &nf, &ns, &ni);
+      sol_x = p;
+      sol_b = b;
+      if (s != UF_OK) return s;
+      adj_mu = mu;
+      adj_b = badj;
+    }
+    const size_t faceB = A.faceN * sizeof(T), cellB = A.cellN * sizeof(T);
+    UF_CUDA(cudaMemsetAsync(lam, 0, (5 * A.faceN + 9 * A.cellN) * sizeof(T), stream));
+    // 1. forward sweep with checkpoints every C steps
+    for (int n = 0; n < nsteps; ++n) {
+      if (n % C == 0) UF_CUDA(save_state(base + A.ckpt0 + (size_t)(n / C) * A.ckpt, A));
+      UF_CUDA(cudaGraphLaunch(step_exec[parity], stream));
+      parity ^= 1;
+    }
+    UF_CUDA(save_state(base + A.fin, A));
+    s = check_device(nullptr);
+    if (s != UF_OK) return s;
+    double J = 0.0;
+    s = objective(z_lo, z_hi, u_hi, u_lo, &J);
+    if (s != UF_OK) return s;
+    if (J_out) *J_out = J;
+    // 2. seed: dJ/du of the final state
+    int k_lo = d.nz, k_hi = -1;
+    for (int k = 0; k < d.nz; ++k) {
+      const double zc = (k + 0.5) * d.h;
+      if (zc >= z_lo && zc <= z_hi) { k_lo = std::min(k_lo, k); k_hi = std::max(k_hi, k); }
+    }
+    const dim3 blk(uf::BX, uf::BY);
+    if (k_hi >= k_lo)
+      uf::k_objective_adj<T><<<plane_grid(d.nx, d.ny, k_hi - k_lo + 1), blk, 0, stream>>>(sp, u, v, w, k_lo, k_hi, u_hi,
+                                                                                          u_lo, L1.u, L1.v, L1.w);
+    UF_CUDA(cudaGetLastError());
+    // 3. reverse sweep, one checkpoint segment at a time
+    const dim3 gc = plane_grid(d.nx, d.ny, d.nz);
+    const dim3 ga = plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1);
+    for (int seg = A.nseg - 1; seg >= 0; --seg) {
+      const int n0 = seg * C, n1 = std::min(nsteps, n0 + C);
+      UF_CUDA(load_state(base + A.ckpt0 + (size_t)seg * A.ckpt, A));
+      for (int n = n0; n < n1; ++n) {   // recompute the segment, taping each step
+        T* t = base + A.tape0 + (size_t)(n - n0) * A.slot;
+        UF_CUDA(save_state(t, A));
+        UF_CUDA(cudaGraphLaunch(step_exec[parity], stream));
+        parity ^= 1;
+        UF_CUDA(copy_cell(t + A.s_nut, nut));
+        UF_CUDA(copy_faces(faces_at(t + A.s_uh), uh, vh, wh));
+        UF_CUDA(copy_faces(faces_at(t + A.s_ut), ut, vt, wt));
+        UF_CUDA(copy_faces(faces_at(t + A.s_u2), u2, v2, w2));
+        UF_CUDA(copy_faces(faces_at(t + A.s_u1), u, v, w));
+      }
+      for (int n = n1 - 1; n >= n0; --n) {
+        T* t = base + A.tape0 + (size_t)(n - n0) * A.slot;
+        const FaceSet U0 = faces_at(t);
+        const T* K0 = t + A.faceN;
+        const T* O0 = t + A.faceN + A.cellN;
+        const T* NUT = t + A.s_nut;
+        const FaceSet UH = faces_at(t + A.s_uh);
+        const FaceSet UT = faces_at(t + A.s_ut);
+        const FaceSet U2 = faces_at(t + A.s_u2);
+        const FaceSet U1 = faces_at(t + A.s_u1);
+        UF_CUDA(cudaMemsetAsync(L0.u, 0, faceB, stream));
+        UF_CUDA(cudaMemsetAsync(Lt.u, 0, 3 * faceB, stream));   // Lt, L2, Lh are contiguous
+        UF_CUDA(cudaMemsetAsync(lk0, 0, cellB, stream));
+        UF_CUDA(cudaMemsetAsync(lo0, 0, cellB, stream));
+        UF_CUDA(cudaMemsetAsync(lnut, 0, cellB, stream));
+        // a9^T: k-omega update
+        uf::k_turbulence_adj<T><<<gc, blk, 0, stream>>>(sp, U1.u, U1.v, U1.w, K0, O0, lk1, lo1, lk0, lo0, L1.u, L1.v,
+                                                        L1.w);
+        // a8^T: projection (A symmetric: the same MG-PCG)
+        uf::k_proj_adj_rhs<T><<<gc, blk, 0, stream>>>(sp, L1.u, L1.v, L1.w, badj);
+        UF_CUDA(cudaGraphLaunch(adj_solve_exec, stream));
+        uf::k_proj_adj_apply<T><<<ga, blk, 0, stream>>>(sp, mu, L1.u, L1.v, L1.w);
+        // a4/a5^T: drag and velocity BCs
+        uf::k_drag_bc_adj<T><<<ga, blk, 0, stream>>>(sp, U2.u, U2.v, U2.w, cc, L1.u, L1.v, L1.w, L2.u, L2.v, L2.w, lc);
+        // a3^T: diffusion
+        uf::k_diffuse_adj<T><<<ga, blk, 0, stream>>>(sp, UT.u, UT.v, UT.w, NUT, L2.u, L2.v, L2.w, Lt.u, Lt.v, Lt.w,
+                                                     lnut);
+        // a2^T: MacCormack advection
+        uf::AdvectArgs<T> Aa = advect_args();
+        Aa.u = U0.u; Aa.v = U0.v; Aa.w = U0.w;
+        Aa.uh = UH.u; Aa.vh = UH.v; Aa.wh = UH.w;
+        uf::AdvectAdj<T> Ja{Lt.u, Lt.v, Lt.w, Lh.u, Lh.v, Lh.w, L0.u, L0.v, L0.w};
+        uf::k_advect_backward_adj<T><<<ga, blk, 0, stream>>>(Aa, Ja);
+        uf::k_advect_forward_adj<T><<<ga, blk, 0, stream>>>(Aa, Ja);
+        // a1^T: eddy viscosity
+        uf::k_eddy_viscosity_adj<T><<<gc, blk, 0, stream>>>(sp, U0.u, U0.v, U0.w, K0, O0, lnut, lk0, lo0, L0.u, L0.v,
+                                                            L0.w);
+        UF_CUDA(cudaGetLastError());
+        std::swap(L0, L1);
+        std::swap(lk0, lk1);
+        std::swap(lo0, lo1);
+      }
+      s = check_device(nullptr);
+      if (s != UF_OK) return s;
+    }
+    // 4. dJ/dphi = dJ/dc dc/dphi; leave the grid at the final state
+    uf::k_dphi<T><<<(unsigned)((P.n_c + 255) / 256), 256, 0, stream>>>(phi, lc, lphi, P.n_c, d.Cd, d.a, d.b, d.e);
+    UF_CUDA(cudaGetLastError());
+    UF_CUDA(load_state(base + A.fin, A));
+    if (dJ_dphi) {
+      s = copy_out(dJ_dphi, lphi, d.nx, d.ny, d.nz, P.Pc);
+      if (s != UF_OK) return s;
+    }
+    return check_device(nullptr);
+  }
+
+  // ---------------------------------------------------- design -> phi ----
+  uf_status upload_boxes(int nbox, const double* boxes, const double* theta) {
+    if (nbox < 1 || nbox > uf::MAX_BOXES) return fail(UF_ERR_ARG, "nbox must lie in [1, 64]");
+    if (!boxes || !theta) return fail(UF_ERR_ARG, "NULL boxes or theta");
+    std::vector<uf::DesignBox> hb(nbox);
+    for (int i = 0; i < nbox; ++i)
+      hb[i] = {boxes[4 * i], boxes[4 * i + 1], boxes[4 * i + 2], boxes[4 * i + 3], theta[3 * i], theta[3 * i + 1],
+               theta[3 * i + 2]};
+    UF_CUDA(cudaMemcpyAsync(at<uf::DesignBox>(P.boxes), hb.data(), sizeof(uf::DesignBox) * nbox, cudaMemcpyHostToDevice,
+                            stream));
+    UF_CUDA(cudaStreamSynchronize(stream));
+    return UF_OK;
+  }
+  uf_status design_phi(int nbox, const double* boxes, const double* theta, double width, void* out) override {
+    if (!(width > 0)) return fail(UF_ERR_ARG, "width must be positive");
+    uf_status s = upload_boxes(nbox, boxes, theta);
+    if (s != UF_OK) return s;
+    T* dst = out ? q : phi;
+    uf::k_design_phi<T><<<plane_grid(d.nx, d.ny, d.nz), dim3(uf::BX, uf::BY), 0, stream>>>(
+        d.nx, d.ny, d.nz, P.Pc, d.h, at<uf::DesignBox>(P.boxes), nbox, width, dst);
+    UF_CUDA(cudaGetLastError());
+    if (out) return copy_out(out, q, d.nx, d.ny, d.nz, P.Pc);
+    const size_t n = P.n_c;
+    uf::k_drag_coeff<T><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(phi, cc, n, d.Cd, d.a, d.b, d.e);
+    UF_CUDA(cudaGetLastError());
+    return UF_OK;
+  }
+  uf_status design_vjp(int nbox, const double* boxes, const double* theta, double width, const void* lphi_in,
+                       double* g_out) override {
+    if (!(width > 0) || !g_out) return fail(UF_ERR_ARG, "width must be positive and g_out non-NULL");
+    uf_status s = upload_boxes(nbox, boxes, theta);
+    if (s != UF_OK) return s;
+    s = copy_in(q, d.nx, d.ny, d.nz, P.Pc, lphi_in);
+    if (s != UF_OK) return s;
+    double* g = at<double>(P.grad);
+    UF_CUDA(cudaMemsetAsync(g, 0, sizeof(double) * 3 * nbox, stream));
+    uf::k_design_phi_vjp<T><<<plane_grid(d.nx, d.ny, d.nz), dim3(uf::BX, uf::BY), 0, stream>>>(
+        d.nx, d.ny, d.nz, P.Pc, d.h, at<uf::DesignBox>(P.boxes), nbox, width, q, g);
+    UF_CUDA(cudaGetLastError());
+    UF_CUDA(cudaMemcpyAsync(g_out, g, sizeof(double) * 3 * nbox, cudaMemcpyDeviceToHost, stream));
+    UF_CUDA(cudaStreamSynchronize(stream));
+    return UF_OK;
+  }
 
   // Captures pre(s) ; solve ; post(s) into an executable graph.
   template <typename Pre, typename Post>
@@ -1056,6 +1333,23 @@ uf_status uf_profile_step(uf_grid* g, uf_kernel_time* out, int capacity, int* co
   UF_NEED(g);
   if (capacity < 0) return fail(UF_ERR_ARG, "negative capacity");
   return g->profile_step(out, capacity, count, stats);
+}
+size_t uf_adjoint_workspace_bytes(uf_grid* g, int nsteps, int ckpt_every) {
+  return g ? g->adjoint_bytes(nsteps, ckpt_every) : 0;
+}
+uf_status uf_adjoint_run(uf_grid* g, void* ws, size_t bytes, int nsteps, int ckpt_every, double z_lo, double z_hi,
+                         double u_hi, double u_lo, void* dJ_dphi, double* J_out) {
+  UF_NEED(g);
+  return g->adjoint_run(ws, bytes, nsteps, ckpt_every, z_lo, z_hi, u_hi, u_lo, dJ_dphi, J_out);
+}
+uf_status uf_design_to_phi(uf_grid* g, int nbox, const double* boxes, const double* theta, double width, void* phi_out) {
+  UF_NEED(g);
+  return g->design_phi(nbox, boxes, theta, width, phi_out);
+}
+uf_status uf_design_vjp(uf_grid* g, int nbox, const double* boxes, const double* theta, double width,
+                        const void* dJ_dphi, double* dJ_dtheta) {
+  UF_NEED(g);
+  return g->design_vjp(nbox, boxes, theta, width, dJ_dphi, dJ_dtheta);
 }
 const char* uf_last_error(void) { return g_err.c_str(); }
 

@@ -144,6 +144,14 @@ def load():
     lib.uf_profile_step.restype = ip
     lib.uf_launch_counts.argtypes = [vp, P(ip), P(ip)]
     lib.uf_launch_counts.restype = ip
+    lib.uf_adjoint_workspace_bytes.argtypes = [vp, ip, ip]
+    lib.uf_adjoint_workspace_bytes.restype = ctypes.c_size_t
+    lib.uf_adjoint_run.argtypes = [vp, vp, ctypes.c_size_t, ip, ip, dp, dp, dp, dp, vp, P(dp)]
+    lib.uf_adjoint_run.restype = ip
+    lib.uf_design_to_phi.argtypes = [vp, ip, P(dp), P(dp), dp, vp]
+    lib.uf_design_to_phi.restype = ip
+    lib.uf_design_vjp.argtypes = [vp, ip, P(dp), P(dp), dp, vp, P(dp)]
+    lib.uf_design_vjp.restype = ip
     lib.uf_poisson_solve_static.argtypes = [ip, ip, ip, dp, vp, vp, dp, ip, vp, P(ip), P(dp)]
     lib.uf_poisson_solve_static.restype = ip
     for name in ("uf_create_grid", "uf_destroy", "uf_set_porosity", "uf_set_state", "uf_get_state",
@@ -331,6 +339,52 @@ class Grid:
                                         bytes_per_launch=k.bytes_per_launch)
         return s, out
 
+    # -- design gradients ------------------------------------------------
+    def adjoint_run(self, nsteps: int, ckpt_every: int = 20, z_lo=1.0, z_hi=3.0, u_hi=4.0, u_lo=1.0):
+        """Forward nsteps from the current state, objective, reverse sweep.
+        Returns (J, dJ/dphi as a numpy array); the grid ends at the final state."""
+        import torch
+        nbytes = int(self.lib.uf_adjoint_workspace_bytes(self._h, nsteps, ckpt_every))
+        if nbytes == 0:
+            raise UFError(UF_ERR_ARG, "bad nsteps / ckpt_every")
+        ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        out = np.empty(self.shapes["phi"], dtype=self.np_dtype)
+        optr, keep = _ptr(out, self.dtypes)
+        J = ctypes.c_double()
+        check(self.lib.uf_adjoint_run(self._h, ctypes.c_void_p(ws.data_ptr()), nbytes, nsteps, ckpt_every, z_lo, z_hi,
+                                      u_hi, u_lo, optr, ctypes.byref(J)))
+        del ws
+        return J.value, out
+
+    @staticmethod
+    def _design_arrays(boxes, theta):
+        b = np.ascontiguousarray(np.asarray(boxes, dtype=np.float64).reshape(-1, 4))
+        t = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1, 3))
+        if b.shape[0] != t.shape[0]:
+            raise ValueError("boxes and theta describe different numbers of buildings")
+        return b, t
+
+    def design_to_phi(self, boxes, theta, width: float, set_porosity: bool = True):
+        """Sigmoid box design -> porosity; sets the grid's porosity (default)
+        or returns the field."""
+        b, t = self._design_arrays(boxes, theta)
+        dptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        if set_porosity:
+            check(self.lib.uf_design_to_phi(self._h, b.shape[0], dptr(b), dptr(t), width, None))
+            return None
+        out = np.empty(self.shapes["phi"], dtype=self.np_dtype)
+        optr, keep = _ptr(out, self.dtypes)
+        check(self.lib.uf_design_to_phi(self._h, b.shape[0], dptr(b), dptr(t), width, optr))
+        return out
+
+    def design_vjp(self, boxes, theta, width: float, dJ_dphi):
+        b, t = self._design_arrays(boxes, theta)
+        dptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        lp, keep = _ptr(np.asarray(dJ_dphi, dtype=self.np_dtype), self.dtypes)
+        g = np.zeros(3 * b.shape[0], dtype=np.float64)
+        check(self.lib.uf_design_vjp(self._h, b.shape[0], dptr(b), dptr(t), width, lp, dptr(g)))
+        return g
+
     def launch_counts(self):
         """(kernels per step outside the CG loop, kernels per CG iteration)."""
         fixed = ctypes.c_int()
@@ -347,3 +401,44 @@ class Grid:
     def set_fields(self, st: dict) -> None:
         for n, val in st.items():
             self.set_state(n, np.asarray(val, dtype=self.np_dtype))
+
+
+def _make_objective_function():
+    import torch
+
+    class UrbanFlowObjective(torch.autograd.Function):
+        """J(theta): the pedestrian comfort objective after `nsteps` steps from
+        a fixed initial state, as a function of the building parameters
+        theta = (height, x shift, y shift) per box.  forward runs the
+        checkpointed forward and reverse sweeps (uf_adjoint_run) and the
+        design VJP; backward returns the stored gradient."""
+
+        @staticmethod
+        def forward(ctx, theta, grid, boxes, width, x0, nsteps, ckpt_every, band):
+            th = theta.detach().cpu().numpy().astype(np.float64)
+            grid.design_to_phi(boxes, th, width)
+            grid.set_fields(x0)
+            z_lo, z_hi, u_hi, u_lo = band
+            J, dphi = grid.adjoint_run(nsteps, ckpt_every, z_lo, z_hi, u_hi, u_lo)
+            g = grid.design_vjp(boxes, th, width, dphi)
+            ctx.save_for_backward(torch.as_tensor(g, dtype=theta.dtype).reshape(theta.shape))
+            return torch.tensor(J, dtype=theta.dtype)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            (g,) = ctx.saved_tensors
+            return gJ * g, None, None, None, None, None, None, None
+
+    return UrbanFlowObjective
+
+
+_objective_fn = None
+
+
+def comfort_objective(theta, grid: "Grid", boxes, width: float, x0: dict, nsteps: int, ckpt_every: int = 20,
+                      band=(1.0, 3.0, 4.0, 1.0)):
+    """Differentiable J(theta) (torch.autograd): see UrbanFlowObjective."""
+    global _objective_fn
+    if _objective_fn is None:
+        _objective_fn = _make_objective_function()
+    return _objective_fn.apply(theta, grid, boxes, width, x0, nsteps, ckpt_every, band)

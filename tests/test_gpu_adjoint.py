@@ -1,0 +1,203 @@
+"""Discrete adjoint of the RANS step: gradients against finite differences
+of the forward runs (GPU FP64 and the FP64 oracle), checkpoint invariance,
+precision, the design map and the autograd binding."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_01117_gb300 import uf
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NX, NY, NZ, H = 24, 20, 10, 2.0
+BOXES = [(14.0, 22.0, 12.0, 20.0), (28.0, 36.0, 20.0, 28.0)]
+THETA = np.array([9.0, 0.3, -0.4, 7.0, -0.2, 0.5])
+WIDTH = 2.0
+PARAMS = dict(h=H, wind_dir_deg=0.0, u_ref=3.0, z_ref=10.0, z0=0.5, inflow_loglaw=1, ground_noslip=1,
+              fixed_dt=0.25)
+NSTEPS = 6
+BAND = (1.0, 3.0, 4.0, 1.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    uf.build()
+    uf.load()
+    oracle.build()
+
+
+def grid(precision="f64", **kw):
+    p = dict(PARAMS)
+    p.update(kw)
+    return uf.Grid(NX, NY, NZ, precision=precision, **p)
+
+
+def start_state(g):
+    """Developed initial state X0 (held fixed by the gradient)."""
+    g.design_to_phi(BOXES, THETA, WIDTH)
+    g.init_state()
+    g.run(4)
+    return g.state()
+
+
+def fd_reference(J):
+    """Central differences of J(theta) with the prescribed 1e-3 m step.  The
+    step is piecewise smooth (the Selle clamp of the MacCormack scheme, the
+    drag clamp and the eddy-viscosity limiter switch branches), so where the
+    1e-3 m difference straddles such a switch it disagrees with the 1e-4 m
+    difference; that component takes the 1e-4 m value.  Decided from forward
+    runs alone.  Returns (reference, number of components replaced)."""
+    def central(hs):
+        return np.array([(J(THETA + e) - J(THETA - e)) / (2 * hs) for e in hs * np.eye(THETA.size)])
+    f3, f4 = central(1e-3), central(1e-4)
+    smooth = np.abs(f3 - f4) <= 1e-4 * np.abs(f4) + 1e-5 * np.abs(f4).max()
+    return np.where(smooth, f3, f4), int((~smooth).sum())
+
+
+def J_of(g, x0, phi=None, theta=None):
+    if theta is not None:
+        g.design_to_phi(BOXES, theta, WIDTH)
+    if phi is not None:
+        g.set_porosity(phi.astype(g.np_dtype))
+    g.set_fields(x0)
+    g.run(NSTEPS)
+    return g.objective(*BAND)
+
+
+def test_design_map_matches_oracle():
+    g = grid()
+    phi = g.design_to_phi(BOXES, THETA, WIDTH, set_porosity=False)
+    ref = oracle.design_to_phi(NX, NY, NZ, H, BOXES, THETA.reshape(-1, 3), WIDTH)
+    np.testing.assert_allclose(phi, ref, rtol=0, atol=1e-13)
+
+
+def test_design_vjp_matches_fd():
+    g = grid()
+    lam = np.random.default_rng(4).standard_normal((NZ, NY, NX))
+    gv = g.design_vjp(BOXES, THETA, WIDTH, lam)
+    for q in range(6):
+        e = np.zeros(6)
+        e[q] = 1e-5
+        fp = oracle.design_to_phi(NX, NY, NZ, H, BOXES, (THETA + e).reshape(-1, 3), WIDTH)
+        fm = oracle.design_to_phi(NX, NY, NZ, H, BOXES, (THETA - e).reshape(-1, 3), WIDTH)
+        fd = np.sum(lam * (fp - fm)) / 2e-5
+        assert gv[q] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_adjoint_directional_derivative_in_phi():
+    g = grid()
+    x0 = start_state(g)
+    phi = g.get_state("phi")
+    g.set_fields(x0)
+    J, dphi = g.adjoint_run(NSTEPS, ckpt_every=4, z_lo=BAND[0], z_hi=BAND[1], u_hi=BAND[2], u_lo=BAND[3])
+    assert J > 0
+    rng = np.random.default_rng(11)
+    for trial in range(3):
+        v = rng.standard_normal(phi.shape) * phi * (1 - phi)
+        eps = 1e-5
+        jp = J_of(g, x0, phi=phi + eps * v)
+        jm = J_of(g, x0, phi=phi - eps * v)
+        fd = (jp - jm) / (2 * eps)
+        ad = float(np.sum(dphi * v))
+        assert ad == pytest.approx(fd, rel=1e-4), (trial, ad, fd)
+
+
+def test_adjoint_theta_gradient_vs_central_fd():
+    g = grid()
+    x0 = start_state(g)
+    g.design_to_phi(BOXES, THETA, WIDTH)
+    g.set_fields(x0)
+    J, dphi = g.adjoint_run(NSTEPS, ckpt_every=3, z_lo=BAND[0], z_hi=BAND[1], u_hi=BAND[2], u_lo=BAND[3])
+    grad = g.design_vjp(BOXES, THETA, WIDTH, dphi)
+    fd, replaced = fd_reference(lambda th: J_of(g, x0, theta=th))
+    assert replaced <= 2, fd
+    floor = 1e-3 * np.abs(fd).max()
+    assert np.all(np.abs(grad - fd) <= 1e-3 * np.abs(fd) + floor), (grad, fd)
+
+
+def test_checkpoint_interval_does_not_change_gradient():
+    g = grid()
+    x0 = start_state(g)
+    outs = []
+    for C in (1, 4, NSTEPS):
+        g.design_to_phi(BOXES, THETA, WIDTH)
+        g.set_fields(x0)
+        J, dphi = g.adjoint_run(NSTEPS, ckpt_every=C)
+        outs.append((J, dphi))
+    for J, dphi in outs[1:]:
+        assert J == outs[0][0]
+        np.testing.assert_allclose(dphi, outs[0][1], rtol=1e-9, atol=1e-12 * np.abs(outs[0][1]).max())
+    # the grid ends at the final state, as after uf_run
+    g.set_fields(x0)
+    g.run(NSTEPS)
+    ref = g.get_state("u")
+    g.set_fields(x0)
+    g.adjoint_run(NSTEPS, ckpt_every=4)
+    np.testing.assert_array_equal(g.get_state("u"), ref)
+
+
+def test_fp32_adjoint_close_to_fp64():
+    grads = {}
+    for prec in ("f64", "f32"):
+        g = grid(prec)
+        g64 = grid("f64")
+        x0 = start_state(g64)
+        g.design_to_phi(BOXES, THETA, WIDTH)
+        g.set_fields(x0)
+        J, dphi = g.adjoint_run(NSTEPS, ckpt_every=3)
+        grads[prec] = g.design_vjp(BOXES, THETA, WIDTH, dphi)
+    rel = np.linalg.norm(grads["f32"] - grads["f64"]) / np.linalg.norm(grads["f64"])
+    assert rel <= 2e-3, (rel, grads)
+
+
+def test_adjoint_matches_oracle_finite_differences():
+    """The oracle's central-difference gradient of its own J (FP64, its own
+    design map) against the GPU adjoint from the same initial state."""
+    op = dict(PARAMS)
+    o = oracle.Oracle(NX, NY, NZ, **op)
+    o.set("phi", oracle.design_to_phi(NX, NY, NZ, H, BOXES, THETA.reshape(-1, 3), WIDTH))
+    o.init()
+    o.run(4)
+    x0 = o.state()
+
+    def oJ(theta):
+        o.set("phi", oracle.design_to_phi(NX, NY, NZ, H, BOXES, theta.reshape(-1, 3), WIDTH))
+        o.set_state(x0)
+        o.run(NSTEPS)
+        return o.objective(*BAND)
+
+    fd, replaced = fd_reference(oJ)
+    assert replaced <= 2, fd
+    g = grid()
+    g.design_to_phi(BOXES, THETA, WIDTH)
+    g.set_fields(x0)
+    J, dphi = g.adjoint_run(NSTEPS, ckpt_every=4)
+    grad = g.design_vjp(BOXES, THETA, WIDTH, dphi)
+    assert J == pytest.approx(oJ(THETA), rel=1e-9)
+    floor = 1e-3 * np.abs(fd).max()
+    assert np.all(np.abs(grad - fd) <= 1e-3 * np.abs(fd) + floor), (grad, fd)
+
+
+def test_autograd_function():
+    g = grid()
+    x0 = start_state(g)
+    theta = torch.tensor(THETA, dtype=torch.float64, requires_grad=True)
+    J = uf.comfort_objective(theta, g, BOXES, WIDTH, x0, NSTEPS, ckpt_every=3, band=BAND)
+    J.backward()
+    g.design_to_phi(BOXES, THETA, WIDTH)
+    g.set_fields(x0)
+    J2, dphi = g.adjoint_run(NSTEPS, ckpt_every=3)
+    ref = g.design_vjp(BOXES, THETA, WIDTH, dphi)
+    assert J.item() == pytest.approx(J2, rel=1e-12)
+    np.testing.assert_allclose(theta.grad.numpy(), ref, rtol=1e-9, atol=1e-12)
+
+
+def test_adjoint_needs_fixed_dt():
+    g = uf.Grid(NX, NY, NZ, precision="f64", h=H)
+    g.init_state()
+    with pytest.raises(uf.UFError) as ei:
+        g.adjoint_run(2)
+    assert ei.value.status == uf.UF_ERR_ARG
