@@ -11,6 +11,9 @@ needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
+The line also carries "adjoint": the adjoint/forward time ratio on the
+128 x 128 x 48 parametric design workload (see adjoint_leg).
+
 Multi-GPU: replicas only (each rank advances its own independent grid; no
 collective in the data path), weak scaling; rank 0 prints one JSON line.
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead.
@@ -147,6 +150,59 @@ def ncu_traffic(kernel_label: str):
             except ValueError:
                 return None
     return None
+
+
+# ---------------------------------------------------------------- adjoint leg
+
+def adjoint_leg():
+    """Adjoint/forward time on the parametric design workload: 128x128x48,
+    12 buildings (H, dx, dy each) mapped to porosity by one-cell logistic
+    ramps, 200 steps at the fixed dt = 0.2 s, checkpoints every 20 steps, FP32
+    fields.  forward = uf_run + uf_objective; adjoint = uf_adjoint_run (its
+    own checkpointed forward sweep, per-segment recompute, reverse sweep),
+    both from the same state and timed on the wall clock with the device
+    synchronised on both sides, after one untimed call of each."""
+    import torch
+    from paper_2204_01117_gb300 import layouts, uf
+    d = layouts.design_lattice()
+    g = uf.Grid(d.nx, d.ny, d.nz, precision="f32", **d.params())
+    g.design_to_phi(d.boxes, d.theta, d.width)
+    g.init_state()
+    x0 = g.state()
+    dphi = torch.empty(g.shapes["phi"], dtype=torch.float32, device="cuda")
+
+    def forward():
+        g.set_fields(x0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        g.run(d.steps, stats=False)
+        J = g.objective()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, J
+
+    def adjoint():
+        g.set_fields(x0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        J, _ = g.adjoint_run(d.steps, d.ckpt_every, out=dphi)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, J
+
+    forward()
+    adjoint()
+    tf, Jf = forward()
+    ta, Ja = adjoint()
+    grad = g.design_vjp(d.boxes, d.theta, d.width, dphi)
+    out = {"workload": f"design lattice {d.nx}x{d.ny}x{d.nz}, h={d.h} m, 12 parametric buildings "
+                       f"(36 parameters), {d.steps} steps at fixed dt={d.fixed_dt} s, checkpoints every "
+                       f"{d.ckpt_every}, FP32 fields + FP64 reductions",
+           "forward_ms": tf * 1e3, "adjoint_ms": ta * 1e3, "ratio": ta / tf,
+           "J": Jf, "J_matches_forward": bool(Ja == Jf),
+           "grad_norm": float(sum(x * x for x in grad)) ** 0.5,
+           "workspace_bytes": int(g.lib.uf_adjoint_workspace_bytes(g._h, d.steps, d.ckpt_every))}
+    g.free_adjoint_workspace()
+    g.close()
+    return out
 
 
 # ---------------------------------------------------------------- oracle arm
@@ -301,6 +357,8 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+    if not args.no_adjoint:
+        line["adjoint"] = adjoint_leg()
     if not args.no_cpu_baseline and world == 1:
         rate, cores, sample, done, dt = oracle_sample(max_seconds=60.0, steps_wanted=1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
@@ -318,6 +376,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

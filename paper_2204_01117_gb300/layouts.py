@@ -203,6 +203,46 @@ def scaled_urban_block(nx, ny, nz, h=2.0, seed=0, wind_dir_deg=0.0, u_ref=3.0, s
                        wind_dir_deg=wind_dir_deg, steps=steps)
 
 
+@dataclass
+class DesignScenario(Scenario):
+    """A parametric design: base footprints and the design parameters of
+    each building.  The porosity comes from the method's design map, not
+    from this module (``phi`` holds open air)."""
+    boxes: np.ndarray = None            # (nbox, 4): x_a, x_b, y_a, y_b of each base footprint [m]
+    theta: np.ndarray = None            # (nbox, 3): height H, x shift, y shift [m]
+    width: float = 2.0                  # logistic ramp width [m]
+    fixed_dt: float = 0.2               # [s]
+    ckpt_every: int = 20
+
+    def params(self) -> dict:
+        d = super().params()
+        d["fixed_dt"] = self.fixed_dt
+        return d
+
+
+def design_lattice(nx=128, ny=128, nz=48, h=2.0, cols=4, rows=3, footprint=20.0, height=(20.0, 40.0),
+                   seed=0, u_ref=3.0, fixed_dt=0.2, steps=200, ckpt_every=20) -> DesignScenario:
+    """cols x rows parametric buildings of square footprint on an even
+    lattice (centre of column c at (c + 1)/(cols + 1) of the domain length,
+    likewise for rows), heights drawn uniformly, shifts zero; log-law
+    inflow along +x; one-cell logistic ramps; the fixed time step of 0.2 s
+    used for the design runs of Sec. 6 ("Avoiding Heat Pockets in Early
+    Design Stages").  Draw order: one height per building, row by row."""
+    rng = SplitMix64(seed)
+    lx, ly = nx * h, ny * h
+    boxes, theta = [], []
+    for r in range(rows):
+        for c in range(cols):
+            cx, cy = lx * (c + 1) / (cols + 1), ly * (r + 1) / (rows + 1)
+            boxes.append((cx - footprint / 2, cx + footprint / 2, cy - footprint / 2, cy + footprint / 2))
+            theta.append((rng.uniform(*height), 0.0, 0.0))
+    return DesignScenario(nx, ny, nz, h, np.ones((nz, ny, nx)), wind_dir_deg=0.0, u_ref=u_ref, z_ref=10.0,
+                          z0=0.5, inflow_loglaw=True, ground_noslip=True, steps=steps,
+                          name=f"design_{nx}x{ny}x{nz}_{cols * rows}b_s{seed}",
+                          boxes=np.array(boxes), theta=np.array(theta), width=h, fixed_dt=fixed_dt,
+                          ckpt_every=ckpt_every)
+
+
 def empty_domain(nx, ny, nz, h=1.0, u_ref=2.0, wind_dir_deg=0.0, ground_noslip=False,
                  loglaw=False) -> Scenario:
     phi = np.ones((nz, ny, nx))
@@ -250,6 +290,8 @@ def config(name: str) -> Scenario:
         return single_box()
     if name == "urban256":        # 256x256x64, FP32 + FP64 reductions, 500 steps
         return urban_block()
+    if name == "design128":       # 128x128x48, 12 parametric buildings, 200 steps
+        return design_lattice()
     if name == "urban512":        # 512x512x128, 1 m cells
         return urban_block(512, 512, 128, h=1.0, n_boxes=400, n_trees=800,
                            height=(5.0, 120.0), u_ref=5.0, steps=1000)

@@ -191,6 +191,18 @@ def workspace_bytes(desc: GridDesc) -> int:
     return int(load().uf_workspace_bytes(ctypes.byref(desc)))
 
 
+def _torch():
+    import torch
+    return torch
+
+
+def _is_tensor(buf) -> bool:
+    try:
+        return isinstance(buf, _torch().Tensor)
+    except ImportError:
+        return False
+
+
 def _ptr(buf, dtype):
     """(pointer, keep-alive) of a torch tensor (device or host) or numpy array."""
     try:
@@ -268,21 +280,29 @@ class Grid:
     def dtypes(self):
         return (self.torch_dtype, self.np_dtype)
 
+    def _arg(self, buf):
+        """Pointer to a numpy array or tensor; a CUDA tensor made on torch's
+        current stream is ordered before the grid's stream uses it."""
+        ptr, keep = _ptr(buf, self.dtypes)
+        if _is_tensor(buf) and buf.is_cuda:
+            self.stream.wait_stream(_torch().cuda.current_stream())
+        return ptr, keep
+
     def set_porosity(self, phi) -> None:
-        ptr, keep = _ptr(phi, self.dtypes)
+        ptr, keep = self._arg(phi)
         check(self.lib.uf_set_porosity(self._h, ptr))
 
     def set_state(self, name: str, value) -> None:
         if np.isscalar(value):
             value = np.full(self.shapes[name], value, dtype=self.np_dtype)
-        ptr, keep = _ptr(value, self.dtypes)
+        ptr, keep = self._arg(value)
         check(self.lib.uf_set_state(self._h, FIELDS[name], ptr))
 
     def get_state(self, name: str, out=None):
         """Returns the field as a numpy array (host), or fills ``out``."""
         if out is None:
             out = np.empty(self.shapes[name], dtype=self.np_dtype)
-        ptr, keep = _ptr(out, self.dtypes)
+        ptr, keep = self._arg(out)
         check(self.lib.uf_get_state(self._h, FIELDS[name], ptr))
         return out
 
@@ -340,21 +360,30 @@ class Grid:
         return s, out
 
     # -- design gradients ------------------------------------------------
-    def adjoint_run(self, nsteps: int, ckpt_every: int = 20, z_lo=1.0, z_hi=3.0, u_hi=4.0, u_lo=1.0):
+    def adjoint_run(self, nsteps: int, ckpt_every: int = 20, z_lo=1.0, z_hi=3.0, u_hi=4.0, u_lo=1.0, out=None):
         """Forward nsteps from the current state, objective, reverse sweep.
-        Returns (J, dJ/dphi as a numpy array); the grid ends at the final state."""
+        Returns (J, dJ/dphi) -- dJ/dphi in ``out`` (a CUDA tensor or numpy
+        array of the grid's precision) or a new numpy array; the grid ends at
+        the final state.  The workspace is kept for the next call of the same
+        size (release it with ``free_adjoint_workspace``)."""
         import torch
         nbytes = int(self.lib.uf_adjoint_workspace_bytes(self._h, nsteps, ckpt_every))
         if nbytes == 0:
             raise UFError(UF_ERR_ARG, "bad nsteps / ckpt_every")
-        ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-        out = np.empty(self.shapes["phi"], dtype=self.np_dtype)
-        optr, keep = _ptr(out, self.dtypes)
+        ws = getattr(self, "_adj_ws", None)
+        if ws is None or ws.numel() < nbytes:
+            self._adj_ws = None
+            ws = self._adj_ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        if out is None:
+            out = np.empty(self.shapes["phi"], dtype=self.np_dtype)
+        optr, keep = self._arg(out)
         J = ctypes.c_double()
         check(self.lib.uf_adjoint_run(self._h, ctypes.c_void_p(ws.data_ptr()), nbytes, nsteps, ckpt_every, z_lo, z_hi,
                                       u_hi, u_lo, optr, ctypes.byref(J)))
-        del ws
         return J.value, out
+
+    def free_adjoint_workspace(self) -> None:
+        self._adj_ws = None
 
     @staticmethod
     def _design_arrays(boxes, theta):
@@ -364,23 +393,24 @@ class Grid:
             raise ValueError("boxes and theta describe different numbers of buildings")
         return b, t
 
-    def design_to_phi(self, boxes, theta, width: float, set_porosity: bool = True):
+    def design_to_phi(self, boxes, theta, width: float, set_porosity: bool = True, out=None):
         """Sigmoid box design -> porosity; sets the grid's porosity (default)
-        or returns the field."""
+        or returns the field (in ``out`` when given: CUDA tensor or numpy)."""
         b, t = self._design_arrays(boxes, theta)
         dptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        if set_porosity:
+        if set_porosity and out is None:
             check(self.lib.uf_design_to_phi(self._h, b.shape[0], dptr(b), dptr(t), width, None))
             return None
-        out = np.empty(self.shapes["phi"], dtype=self.np_dtype)
-        optr, keep = _ptr(out, self.dtypes)
+        if out is None:
+            out = np.empty(self.shapes["phi"], dtype=self.np_dtype)
+        optr, keep = self._arg(out)
         check(self.lib.uf_design_to_phi(self._h, b.shape[0], dptr(b), dptr(t), width, optr))
         return out
 
     def design_vjp(self, boxes, theta, width: float, dJ_dphi):
         b, t = self._design_arrays(boxes, theta)
         dptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        lp, keep = _ptr(np.asarray(dJ_dphi, dtype=self.np_dtype), self.dtypes)
+        lp, keep = self._arg(dJ_dphi if _is_tensor(dJ_dphi) else np.asarray(dJ_dphi, dtype=self.np_dtype))
         g = np.zeros(3 * b.shape[0], dtype=np.float64)
         check(self.lib.uf_design_vjp(self._h, b.shape[0], dptr(b), dptr(t), width, lp, dptr(g)))
         return g
@@ -400,45 +430,79 @@ class Grid:
 
     def set_fields(self, st: dict) -> None:
         for n, val in st.items():
-            self.set_state(n, np.asarray(val, dtype=self.np_dtype))
+            self.set_state(n, val if _is_tensor(val) else np.asarray(val, dtype=self.np_dtype))
 
 
-def _make_objective_function():
+def _make_functions():
     import torch
 
-    class UrbanFlowObjective(torch.autograd.Function):
-        """J(theta): the pedestrian comfort objective after `nsteps` steps from
-        a fixed initial state, as a function of the building parameters
-        theta = (height, x shift, y shift) per box.  forward runs the
-        checkpointed forward and reverse sweeps (uf_adjoint_run) and the
-        design VJP; backward returns the stored gradient."""
+    class ComfortObjective(torch.autograd.Function):
+        """J(phi): the pedestrian comfort objective after `nsteps` steps from a
+        fixed initial state x0, as a function of the porosity field phi.
+        forward runs the steps (uf_run) and the objective (uf_objective);
+        backward re-runs the checkpointed forward and the discrete adjoint
+        (uf_adjoint_run) and returns dJ/dphi on the device."""
 
         @staticmethod
-        def forward(ctx, theta, grid, boxes, width, x0, nsteps, ckpt_every, band):
-            th = theta.detach().cpu().numpy().astype(np.float64)
-            grid.design_to_phi(boxes, th, width)
+        def forward(ctx, phi, grid, x0, nsteps, ckpt_every, band):
+            phi = phi.detach().contiguous()
+            grid.set_porosity(phi)
             grid.set_fields(x0)
-            z_lo, z_hi, u_hi, u_lo = band
-            J, dphi = grid.adjoint_run(nsteps, ckpt_every, z_lo, z_hi, u_hi, u_lo)
-            g = grid.design_vjp(boxes, th, width, dphi)
-            ctx.save_for_backward(torch.as_tensor(g, dtype=theta.dtype).reshape(theta.shape))
-            return torch.tensor(J, dtype=theta.dtype)
+            grid.run(nsteps, stats=False)
+            J = grid.objective(*band)
+            ctx.save_for_backward(phi)
+            ctx.grid, ctx.x0, ctx.nsteps, ctx.ckpt_every, ctx.band = grid, x0, nsteps, ckpt_every, band
+            return torch.tensor(J, dtype=torch.float64, device=phi.device)
 
         @staticmethod
         def backward(ctx, gJ):
-            (g,) = ctx.saved_tensors
-            return gJ * g, None, None, None, None, None, None, None
+            (phi,) = ctx.saved_tensors
+            g = ctx.grid
+            g.set_porosity(phi)
+            g.set_fields(ctx.x0)
+            dphi = torch.empty_like(phi)
+            g.adjoint_run(ctx.nsteps, ctx.ckpt_every, *ctx.band, out=dphi)
+            return gJ.to(dphi.dtype) * dphi, None, None, None, None, None
 
-    return UrbanFlowObjective
+    class DesignPorosity(torch.autograd.Function):
+        """phi(theta): porosity of the logistic-box design (uf_design_to_phi);
+        backward is uf_design_vjp."""
+
+        @staticmethod
+        def forward(ctx, theta, grid, boxes, width):
+            th = theta.detach().cpu().numpy().astype(np.float64)
+            phi = torch.empty(grid.shapes["phi"], dtype=grid.torch_dtype, device="cuda")
+            grid.design_to_phi(boxes, th, width, out=phi)
+            ctx.grid, ctx.boxes, ctx.width, ctx.th = grid, boxes, width, th
+            ctx.like = (theta.dtype, theta.device)
+            return phi
+
+        @staticmethod
+        def backward(ctx, gphi):
+            g = ctx.grid.design_vjp(ctx.boxes, ctx.th, ctx.width, gphi.contiguous().to(ctx.grid.torch_dtype))
+            dtype, device = ctx.like
+            return torch.as_tensor(g).reshape(ctx.th.shape).to(dtype=dtype, device=device), None, None, None
+
+    return ComfortObjective, DesignPorosity
 
 
-_objective_fn = None
+_functions = None
 
 
-def comfort_objective(theta, grid: "Grid", boxes, width: float, x0: dict, nsteps: int, ckpt_every: int = 20,
-                      band=(1.0, 3.0, 4.0, 1.0)):
-    """Differentiable J(theta) (torch.autograd): see UrbanFlowObjective."""
-    global _objective_fn
-    if _objective_fn is None:
-        _objective_fn = _make_objective_function()
-    return _objective_fn.apply(theta, grid, boxes, width, x0, nsteps, ckpt_every, band)
+def _fns():
+    global _functions
+    if _functions is None:
+        _functions = _make_functions()
+    return _functions
+
+
+def comfort_objective(phi, grid: "Grid", x0: dict, nsteps: int, ckpt_every: int = 20, band=(1.0, 3.0, 4.0, 1.0)):
+    """Differentiable J(phi) (torch.autograd): see ComfortObjective.  phi is a
+    CUDA tensor of the grid's precision and shape (nz, ny, nx)."""
+    return _fns()[0].apply(phi, grid, x0, nsteps, ckpt_every, band)
+
+
+def design_porosity(theta, grid: "Grid", boxes, width: float):
+    """Differentiable phi(theta) (torch.autograd): theta holds (H, dx, dy) per
+    box, as a float64 tensor of shape (nbox, 3) or (3 * nbox,)."""
+    return _fns()[1].apply(theta, grid, boxes, width)

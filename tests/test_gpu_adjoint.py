@@ -182,17 +182,37 @@ def test_adjoint_matches_oracle_finite_differences():
 
 
 def test_autograd_function():
+    """theta -> phi -> J through the two autograd Functions, on device tensors:
+    J equals the forward objective, theta.grad the adjoint gradient."""
     g = grid()
     x0 = start_state(g)
-    theta = torch.tensor(THETA, dtype=torch.float64, requires_grad=True)
-    J = uf.comfort_objective(theta, g, BOXES, WIDTH, x0, NSTEPS, ckpt_every=3, band=BAND)
+    theta = torch.tensor(THETA.reshape(-1, 3), dtype=torch.float64, requires_grad=True)
+    phi = uf.design_porosity(theta, g, BOXES, WIDTH)
+    assert phi.is_cuda and phi.dtype == torch.float64
+    np.testing.assert_allclose(phi.detach().cpu().numpy(), g.design_to_phi(BOXES, THETA, WIDTH, set_porosity=False),
+                               rtol=0, atol=0)
+    J = uf.comfort_objective(phi, g, x0, NSTEPS, ckpt_every=3, band=BAND)
     J.backward()
     g.design_to_phi(BOXES, THETA, WIDTH)
     g.set_fields(x0)
-    J2, dphi = g.adjoint_run(NSTEPS, ckpt_every=3)
+    J2, dphi = g.adjoint_run(NSTEPS, ckpt_every=3, z_lo=BAND[0], z_hi=BAND[1], u_hi=BAND[2], u_lo=BAND[3])
     ref = g.design_vjp(BOXES, THETA, WIDTH, dphi)
     assert J.item() == pytest.approx(J2, rel=1e-12)
-    np.testing.assert_allclose(theta.grad.numpy(), ref, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(theta.grad.numpy().ravel(), ref, rtol=1e-9, atol=1e-12)
+
+
+def test_autograd_phi_gradient_on_device():
+    """dJ/dphi from backward lands on the device and equals uf_adjoint_run's."""
+    g = grid()
+    x0 = start_state(g)
+    phi = torch.tensor(g.get_state("phi"), device="cuda", requires_grad=True)
+    J = uf.comfort_objective(phi, g, x0, 4, ckpt_every=2, band=BAND)
+    (gphi,) = torch.autograd.grad(2.0 * J, phi)
+    assert gphi.is_cuda
+    g.set_porosity(phi.detach())
+    g.set_fields(x0)
+    _, dphi = g.adjoint_run(4, ckpt_every=2, z_lo=BAND[0], z_hi=BAND[1], u_hi=BAND[2], u_lo=BAND[3])
+    np.testing.assert_allclose(gphi.cpu().numpy(), 2.0 * dphi, rtol=1e-12, atol=0)
 
 
 def test_adjoint_needs_fixed_dt():

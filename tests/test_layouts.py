@@ -52,3 +52,22 @@ def test_urban_block_statistics():
     assert np.all(sc.phi[:, :, :12] == 1.0) and np.all(sc.phi[:, :, -12:] == 1.0)
     again = layouts.urban_block(128, 128, 32, n_boxes=10, n_trees=15, seed=3)
     assert np.array_equal(sc.phi, again.phi)
+
+
+def test_design_lattice_workload():
+    d = layouts.design_lattice()
+    assert (d.nx, d.ny, d.nz, d.h) == (128, 128, 48, 2.0)
+    assert d.boxes.shape == (12, 4) and d.theta.shape == (12, 3)
+    # square 20 m footprints centred on the 4 x 3 lattice
+    np.testing.assert_allclose(d.boxes[:, 1] - d.boxes[:, 0], 20.0)
+    np.testing.assert_allclose(d.boxes[:, 3] - d.boxes[:, 2], 20.0)
+    cx = 0.5 * (d.boxes[:, 0] + d.boxes[:, 1])
+    cy = 0.5 * (d.boxes[:, 2] + d.boxes[:, 3])
+    np.testing.assert_allclose(sorted(set(np.round(cx, 6))), [256 * c / 5 for c in (1, 2, 3, 4)])
+    np.testing.assert_allclose(sorted(set(np.round(cy, 6))), [256 * r / 4 for r in (1, 2, 3)])
+    assert np.all((d.theta[:, 0] >= 20.0) & (d.theta[:, 0] < 40.0))
+    assert np.all(d.theta[:, 1:] == 0.0)
+    assert d.params()["fixed_dt"] == 0.2 and d.width == d.h
+    # seeded: same seed, same heights; another seed, other heights
+    assert np.array_equal(layouts.design_lattice().theta, d.theta)
+    assert not np.array_equal(layouts.design_lattice(seed=1).theta, d.theta)
