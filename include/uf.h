@@ -208,7 +208,8 @@ uf_status uf_launch_counts(uf_grid* g, int* fixed, int* per_iter);
 
 /* ---- Discrete adjoint and design gradients ----------------------------
  * The paper obtains design gradients by forward differences, N+1 forward
- * simulations per gradient (Sec. 5, "Gradient-descent"; Sec. 6.2); these
+ * simulations per gradient (Sec. 4, "Automatic Design Optimization";
+ * Sec. 6); these
  * entry points give the same gradient from one forward and one reverse
  * sweep: the hand-written transpose of every sub-step of uf_step (a1-a9 in
  * reverse; the pressure solve is self-adjoint because A is symmetric) and of
@@ -251,6 +252,80 @@ uf_status uf_design_to_phi(uf_grid* g, int nbox, const double* boxes, const doub
  * Synchronises. */
 uf_status uf_design_vjp(uf_grid* g, int nbox, const double* boxes, const double* theta, double width,
                         const void* dJ_dphi, double* dJ_dtheta);
+
+/* ---- Launch tuning -----------------------------------------------------
+ * Two knobs of the multigrid-preconditioned solve change only its speed, not
+ * the iteration it computes: where the single-block shared-memory tail of
+ * the V-cycle starts (the multigrid depth handled by per-level kernels) and
+ * how many z planes each block of a per-level kernel marches over (the tile
+ * depth).  Other preconditioners ignore them.  Results stay equal up to the
+ * order of FP64 partial sums. */
+#define UF_MAX_LEVELS 16
+typedef struct {
+  int tail_level;             /* first level of the tail; 0 = automatic (the
+                                 shallowest level whose levels fit 64 KB of
+                                 shared memory); values above the coarsest
+                                 level or below the automatic one are clamped */
+  int march_zc[UF_MAX_LEVELS];/* z planes per block of level l; 0 = automatic;
+                                 otherwise even, 2..64 */
+} uf_tuning;
+
+/* The knobs in use, resolved (no zeros).  levels: number of MG levels. */
+uf_status uf_get_tuning(uf_grid* g, uf_tuning* out, int* levels);
+
+/* Sets the knobs (NULL: back to automatic) and drops the captured graphs,
+ * which are rebuilt on the next call that needs them. */
+uf_status uf_set_tuning(uf_grid* g, const uf_tuning* t);
+
+/* Autotuner: times `reps` pressure solves of a fixed synthetic right-hand
+ * side from a zero guess for each candidate (tail level x uniform tile
+ * depth), keeps the fastest and returns it in *chosen (may be NULL) with its
+ * mean solve time in *best_ms (may be NULL).  Uses only the grid's scratch
+ * buffers: the state is untouched.  Synchronises. */
+uf_status uf_autotune(uf_grid* g, int reps, uf_tuning* chosen, double* best_ms);
+
+/* ---- Batched execution ---------------------------------------------------
+ * Many independent grids -- design variants, wind directions, uneven sizes --
+ * advance together: every phase of the step (a0-a9) is one persistent launch
+ * over a work list of (instance, tile) items, sized to the SMs, and one
+ * captured CUDA graph holds the whole step, with a single conditional WHILE
+ * node for all instances' CG loops (instances that have converged skip their
+ * items until the last one has).  Each instance computes exactly what it
+ * computes alone with the same tuning.  Instances share the precision, the
+ * MG preconditioner and the smoother. */
+typedef struct uf_batch uf_batch;
+
+#define UF_MAX_BATCH 64
+
+/* Bytes of the device workspace of a batch of n (<= UF_MAX_BATCH) grids:
+ * every grid's uf_workspace_bytes plus the batch's work lists. 0 on error. */
+size_t uf_batch_workspace_bytes(int n, const uf_grid_desc* descs);
+
+/* Creates the batch and its n grids inside d_workspace (caller-owned, as for
+ * uf_create_grid); all work runs on `stream`. */
+uf_status uf_batch_create(int n, const uf_grid_desc* descs, void* d_workspace, size_t bytes, void* cuda_stream,
+                          uf_batch** out);
+
+/* Handle of instance i, owned by the batch (do not uf_destroy it): set its
+ * porosity and state, read fields, evaluate objectives, tune it. */
+uf_status uf_batch_grid(uf_batch* b, int i, uf_grid** out);
+
+/* nsteps batched steps of every instance (each needs a state).  stats: NULL
+ * or n entries, filled after the last step (synchronises).  Errors of any
+ * instance are reported (the first one wins). */
+uf_status uf_batch_run(uf_batch* b, int nsteps, uf_step_stats* stats);
+
+/* Kernel launches of one batched step: *fixed outside the CG loop and
+ * *per_iter per CG iteration of the slowest instance. */
+uf_status uf_batch_launch_counts(uf_batch* b, int* fixed, int* per_iter);
+
+/* Autotunes per size class: instances whose grids have the same multigrid
+ * hierarchy shape share one tuning, chosen by uf_autotune on the first of
+ * them; the batch graphs are rebuilt.  classes: number of size classes
+ * (may be NULL). */
+uf_status uf_batch_autotune(uf_batch* b, int reps, int* classes);
+
+uf_status uf_batch_destroy(uf_batch* b);
 
 /* ---- Pressure solve without any device allocation ---------------------
  * The paper has no counterpart to this entry point; it exists for callers

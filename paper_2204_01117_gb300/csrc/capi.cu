@@ -17,7 +17,7 @@
 #include <vector>
 
 #include "../../include/uf.h"
-#include "mg_fused.cuh"
+#include "grid_base.cuh"
 #include "adjoint_kernels.cuh"
 
 namespace {
@@ -102,6 +102,10 @@ bool desc_valid(const uf_grid_desc* d, std::string* why) {
 }
 
 // Host-side summary of a grid's buffers (offsets into the workspace).
+struct Plan;
+size_t tail_bytes(const Plan& P, int lt);
+void plan_tail(Plan& P, int lt);
+
 struct Plan {
   int T_bytes;
   int nx, ny, nz, Pu, Pc;
@@ -110,6 +114,8 @@ struct Plan {
   int coarse_n;
   // offsets
   size_t u, v, w, uh, vh, wh, ut, vt, wt, u2, v2, w2, k0, k1, o0, o1, cc, phi, nut, p, b, r, r2, z, q, d0, d1;
+  int nl;                  // multigrid levels in use (1 without MG)
+  int auto_tail_level;     // shallowest level whose tail fits the shared-memory budget
   int tail_level;          // first level run by the shared-memory tail kernel
   size_t tail_smem;        // its dynamic shared memory (bytes)
   std::vector<int> tail_off;
@@ -156,27 +162,15 @@ Plan make_plan(const uf_grid_desc* d) {
   P.coarse_n = mg ? cl.nx * cl.ny * cl.nz : 0;
   // tail: deepest suffix of levels (never the finest) whose three bordered
   // arrays per level fit the shared-memory budget
-  P.tail_level = (int)nl - 1;
-  auto bordered = [&](int m) {
-    return (size_t)(P.levels[m].nx + 2) * (P.levels[m].ny + 2) * (P.levels[m].nz + 2);
-  };
+  P.nl = (int)nl;
+  P.auto_tail_level = (int)nl - 1;
   if (mg) {
     for (int l = (int)nl - 1; l >= 1; --l) {
-      size_t bytes = 0;
-      for (int m = l; m < (int)nl; ++m) bytes += 3 * bordered(m) * tb;
-      if (bytes > kTailSmemBudget) break;
-      P.tail_level = l;
+      if (tail_bytes(P, l) > kTailSmemBudget) break;
+      P.auto_tail_level = l;
     }
-    P.tail_off.assign(nl, 0);
-    size_t off = 0;
-    for (int m = P.tail_level; m < (int)nl; ++m) {
-      P.tail_off[m] = (int)off;
-      off += 3 * bordered(m);
-    }
-    P.tail_smem = off * tb;
-  } else {
-    P.tail_smem = 0;
   }
+  plan_tail(P, P.auto_tail_level);
   P.prof = L.take((size_t)d->nz * tb);
   P.dt = L.take(8);
   P.dtT = L.take(8);
@@ -188,6 +182,29 @@ Plan make_plan(const uf_grid_desc* d) {
   P.grad = L.take(sizeof(double) * 3 * uf::MAX_BOXES);
   P.total = L.off + 256;
   return P;
+}
+
+// Shared memory of a tail starting at level lt: three bordered arrays per level.
+size_t tail_bytes(const Plan& P, int lt) {
+  size_t n = 0;
+  for (int m = lt; m < P.nl; ++m)
+    n += 3 * (size_t)(P.levels[m].nx + 2) * (P.levels[m].ny + 2) * (P.levels[m].nz + 2);
+  return n * P.T_bytes;
+}
+
+void plan_tail(Plan& P, int lt) {
+  P.tail_level = lt;
+  P.tail_off.assign(P.nl, 0);
+  if (P.coarse_n == 0) {
+    P.tail_smem = 0;
+    return;
+  }
+  size_t off = 0;
+  for (int m = lt; m < P.nl; ++m) {
+    P.tail_off[m] = (int)off;
+    off += 3 * (size_t)(P.levels[m].nx + 2) * (P.levels[m].ny + 2) * (P.levels[m].nz + 2);
+  }
+  P.tail_smem = off * P.T_bytes;
 }
 
 // Dense operator of a level (compact order i + nx (j + ny k)).
@@ -271,26 +288,6 @@ dim3 chunk_grid(int lx, int ly, int lz, int* zc) {
 void uf_internal_set_last_error(const char* msg) { g_err = msg ? msg : ""; }
 
 // ======================================================================
-struct uf_grid {
-  virtual ~uf_grid() {}
-  virtual uf_status set_porosity(const void*) = 0;
-  virtual uf_status set_state(int, const void*) = 0;
-  virtual uf_status get_state(int, void*) = 0;
-  virtual uf_status init_state() = 0;
-  virtual uf_status step(uf_step_stats*) = 0;
-  virtual uf_status run(int, uf_step_stats*) = 0;
-  virtual uf_status objective(double, double, double, double, double*) = 0;
-  virtual uf_status divergence(double*) = 0;
-  virtual uf_status apply_poisson(const void*, void*) = 0;
-  virtual uf_status poisson_solve(const void*, int*, double*) = 0;
-  virtual int last_launches() = 0;
-  virtual uf_status launch_counts(int*, int*) = 0;
-  virtual uf_status profile_step(uf_kernel_time*, int, int*, uf_step_stats*) = 0;
-  virtual size_t adjoint_bytes(int, int) = 0;
-  virtual uf_status adjoint_run(void*, size_t, int, int, double, double, double, double, void*, double*) = 0;
-  virtual uf_status design_phi(int, const double*, const double*, double, void*) = 0;
-  virtual uf_status design_vjp(int, const double*, const double*, double, const void*, double*) = 0;
-};
 
 namespace {
 
@@ -477,22 +474,35 @@ class GridImpl final : public uf_grid {
   double tb() const { return (double)sizeof(T); }
 
 
+  // The dynamic shared-memory limit is an attribute of the kernel, shared by
+  // every grid in the process: raise it to the device's opt-in maximum (each
+  // launch still asks for its own size), never to one grid's size, which
+  // would fail the launches of grids with larger tails.
   cudaError_t set_smem_limits() {
-    cudaError_t e = cudaSuccess;
-    auto lim = [&](const void* f, size_t bytes) {
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess && P.tail_smem > (size_t)optin) return cudaErrorInvalidValue;
+    auto lim = [&](const void* f) {
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     };
-    lim((const void*)uf::k_mg_tail<T, uf::SM_JACOBI>, std::max<size_t>(P.tail_smem, 1));
-    lim((const void*)uf::k_mg_tail<T, uf::SM_RBGS>, std::max<size_t>(P.tail_smem, 1));
+    lim((const void*)uf::k_mg_tail<T, uf::SM_JACOBI>);
+    lim((const void*)uf::k_mg_tail<T, uf::SM_RBGS>);
     return e;
   }
 
-  // z-marching grid: 32 x 8 columns, zc planes (even) per block, zc chosen
-  // so that the level still gives a few blocks per SM.
-  static dim3 march_grid(const uf::Level<T>& L, int* zc) {
+  // z-marching grid of level l: 32 x 8 columns, zc planes (even) per block;
+  // by default zc is chosen so that the level still gives a few blocks per
+  // SM, else it is the tuned value.
+  int march_zc_tuned[uf::MAX_LEVELS] = {0};
+  dim3 march_grid(int l, int* zc) const {
+    const uf::Level<T>& L = lv[l];
     const int bx = (L.nx + uf::TX - 1) / uf::TX, by = (L.ny + uf::TY - 1) / uf::TY;
-    int z = 16;
-    while (z > 2 && (long)bx * by * ((L.nz + z - 1) / z) < 456) z /= 2;
+    int z = march_zc_tuned[l];
+    if (z <= 0) {
+      z = 16;
+      while (z > 2 && (long)bx * by * ((L.nz + z - 1) / z) < 456) z /= 2;
+    }
     *zc = z;
     return dim3(bx, by, (L.nz + z - 1) / z);
   }
@@ -507,7 +517,7 @@ class GridImpl final : public uf_grid {
     for (int l = 0; l < lt; ++l) {
       const std::string sl = std::to_string(l);
       int zc;
-      const dim3 g = march_grid(lv[l], &zc);
+      const dim3 g = march_grid(l, &zc);
       if (l == 0 && mode == 1)
         L(s, "mg_down_cg_L0", (7 * Nl(0) + Nl(1)) * tb(), [&] {
           uf::k_mg_down<T, SM, true><<<g, uf::FT, 0, s>>>(lv[0], lv[1], om, zc, sol_x, d0, d1, q, partials, st, cond,
@@ -524,7 +534,7 @@ class GridImpl final : public uf_grid {
     for (int l = lt - 1; l >= 0; --l) {
       const std::string sl = std::to_string(l);
       int zc;
-      const dim3 g = march_grid(lv[l], &zc);
+      const dim3 g = march_grid(l, &zc);
       if (l == 0)
         L(s, "mg_up_L0", (3 * Nl(0) + Nl(1)) * tb(), [&] {
           uf::k_mg_up<T, SM, true><<<g, uf::FT, 0, s>>>(lv[0], lv[1], om, zc, z, mode, partials, st);
@@ -565,7 +575,7 @@ class GridImpl final : public uf_grid {
   void rec_cg_iter(cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
     if (d.precond == UF_PRECOND_MG) {
       int zc;
-      const dim3 g = march_grid(lv[0], &zc);
+      const dim3 g = march_grid(0, &zc);
       L(s, "cg_dir_q", 4 * N() * tb(), [&] {
         uf::k_cg_dir_q<T><<<g, uf::FT, 0, s>>>(lv[0], zc, z, d0, d1, q, partials, st);
       });
@@ -594,6 +604,8 @@ class GridImpl final : public uf_grid {
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
     UF_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cgraph, &deps, nullptr, &ndeps));
+    if (cs != cudaStreamCaptureStatusActive)   // a launch before this point failed
+      return fail(UF_ERR_CUDA, std::string("graph capture invalidated: ") + cudaGetErrorString(cudaGetLastError()));
     cudaGraphNodeParams np = {};
     np.type = cudaGraphNodeTypeConditional;
     np.conditional.handle = cond;
@@ -1028,6 +1040,172 @@ class GridImpl final : public uf_grid {
     return UF_OK;
   }
 
+  // Drops every captured graph (after a change of the launch tuning).
+  void drop_graphs() {
+    for (auto& e : step_exec)
+      if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+    if (init_exec) { cudaGraphExecDestroy(init_exec); init_exec = nullptr; }
+    if (solve_exec) { cudaGraphExecDestroy(solve_exec); solve_exec = nullptr; }
+    if (adj_solve_exec) { cudaGraphExecDestroy(adj_solve_exec); adj_solve_exec = nullptr; }
+    adj_mu = adj_b = nullptr;
+  }
+
+  // Tail starting at level lt (clamped to [automatic, coarsest]).
+  uf_status set_tail_level(int lt) {
+    if (d.precond != UF_PRECOND_MG) return UF_OK;
+    lt = std::min(std::max(lt, P.auto_tail_level), P.nl - 1);
+    plan_tail(P, lt);
+    for (int l = 0; l < P.nl; ++l) tail.off[l] = P.tail_off[l];
+    tail.lt = lt;
+    UF_CUDA(set_smem_limits());
+    return UF_OK;
+  }
+
+  uf_status get_tuning(uf_tuning* t, int* levels) override {
+    if (!t) return fail(UF_ERR_ARG, "NULL output");
+    std::memset(t, 0, sizeof(*t));
+    t->tail_level = P.tail_level;
+    for (int l = 0; l < P.nl && l < UF_MAX_LEVELS; ++l) {
+      int zc;
+      march_grid(l, &zc);
+      t->march_zc[l] = d.precond == UF_PRECOND_MG ? zc : 0;
+    }
+    if (levels) *levels = P.nl;
+    return UF_OK;
+  }
+
+  uf_status set_tuning(const uf_tuning* t) override {
+    if (t)
+      for (int l = 0; l < UF_MAX_LEVELS; ++l) {
+        const int z = t->march_zc[l];
+        if (z != 0 && (z < 2 || z > 64 || (z & 1))) return fail(UF_ERR_ARG, "march_zc must be 0 or even in [2, 64]");
+      }
+    drop_graphs();
+    for (int l = 0; l < uf::MAX_LEVELS; ++l) march_zc_tuned[l] = t ? t->march_zc[l] : 0;
+    return set_tail_level(t && t->tail_level > 0 ? t->tail_level : P.auto_tail_level);
+  }
+
+  // Autotuner: candidates = tail level (automatic and up to two levels
+  // deeper) x a uniform tile depth (automatic, 2, 4, 8); each is timed over
+  // `reps` solves of a synthetic right-hand side from a zero guess, with the
+  // unknown and the right-hand side in scratch buffers (ut, uh) that no step
+  // keeps between steps.
+  uf_status autotune(int reps, uf_tuning* chosen, double* best_ms) override {
+    if (reps < 1) return fail(UF_ERR_ARG, "reps >= 1 required");
+    if (d.precond != UF_PRECOND_MG) {
+      if (chosen) get_tuning(chosen, nullptr);
+      if (best_ms) *best_ms = 0.0;
+      return UF_OK;
+    }
+    int zc0;
+    dim3 g0 = chunk_grid(d.nx, d.ny, d.nz, &zc0);
+    uf::k_tune_rhs<T><<<g0, dim3(uf::BX, uf::BY), 0, stream>>>(lv[0], uh, zc0);
+    UF_CUDA(cudaGetLastError());
+    cudaEvent_t e0, e1;
+    UF_CUDA(cudaEventCreate(&e0));
+    UF_CUDA(cudaEventCreate(&e1));
+    struct Cand {
+      int lt, zc;
+    };
+    std::vector<Cand> cands;
+    for (int lt = P.auto_tail_level; lt <= std::min(P.nl - 1, P.auto_tail_level + 2); ++lt)
+      for (int zc : {0, 2, 4, 8}) cands.push_back({lt, zc});
+    double best = 1e300;
+    uf_tuning best_t;
+    uf_status rs = UF_OK;
+    for (const Cand& c : cands) {
+      uf_tuning t;
+      std::memset(&t, 0, sizeof(t));
+      t.tail_level = c.lt;
+      for (int l = 0; l < UF_MAX_LEVELS; ++l) t.march_zc[l] = c.zc;
+      rs = set_tuning(&t);
+      if (rs != UF_OK) break;
+      cudaGraphExec_t ex = nullptr;
+      sol_x = ut;
+      sol_b = uh;
+      int nf, ns, ni;
+      auto pre = [&](cudaStream_t s2) {
+        cudaMemsetAsync(ut, 0, P.n_u * sizeof(T), s2);
+        int zc;
+        dim3 g = chunk_grid(d.nx, d.ny, d.nz, &zc);
+        uf::k_solve_reset<T><<<g, dim3(uf::BX, uf::BY), 0, s2>>>(lv[0], uh, zc, partials, st);
+        rec_count++;
+      };
+      rs = capture(&ex, pre, [&](cudaStream_t) {}, &nf, &ns, &ni);
+      sol_x = p;
+      sol_b = b;
+      if (rs != UF_OK) break;
+      cudaError_t e = cudaGraphLaunch(ex, stream);   // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(ex, stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      cudaGraphExecDestroy(ex);
+      if (e != cudaSuccess) {
+        rs = fail(UF_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+        break;
+      }
+      const double mean = ms / reps;
+      if (mean < best) {
+        best = mean;
+        get_tuning(&best_t, nullptr);
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rs != UF_OK) return rs;
+    rs = check_device(nullptr);
+    if (rs != UF_OK) return rs;
+    rs = set_tuning(&best_t);
+    if (rs != UF_OK) return rs;
+    if (chosen) *chosen = best_t;
+    if (best_ms) *best_ms = best;
+    return UF_OK;
+  }
+
+  // ------------------------------------------------------------ batch support
+  const uf_grid_desc& desc() const override { return d; }
+  bool has_state() const override { return have_state; }
+  void advanced(int nsteps) override { parity ^= (nsteps & 1); }
+  uf_status read_status(uf_step_stats* out) override { return check_device(out); }
+
+  void fill_view(void* vp) override {
+    GridView<T>& V = *reinterpret_cast<GridView<T>*>(vp);
+    std::memset(&V, 0, sizeof(V));
+    V.d = d;
+    V.sp = sp;
+    V.adv = advect_args();
+    V.u = u; V.v = v; V.w = w; V.uh = uh; V.vh = vh; V.wh = wh; V.ut = ut; V.vt = vt; V.wt = wt;
+    V.u2 = u2; V.v2 = v2; V.w2 = w2; V.cc = cc; V.nut = nut; V.p = p; V.b = b; V.z = z; V.q = q;
+    V.d0 = d0; V.d1 = d1;
+    V.kb[0] = kb[0]; V.kb[1] = kb[1]; V.ob[0] = ob[0]; V.ob[1] = ob[1];
+    V.parity = parity;
+    V.n_u = P.n_u; V.n_v = P.n_v; V.n_w = P.n_w;
+    V.nl = (int)lv.size();
+    for (int l = 0; l < V.nl; ++l) {
+      V.lv[l] = lv[l];
+      int zc;
+      const dim3 g = march_grid(l, &zc);
+      V.march_g[l][0] = g.x; V.march_g[l][1] = g.y; V.march_g[l][2] = g.z;
+      V.march_zc[l] = zc;
+    }
+    V.tail_level = P.tail_level;
+    V.tail = tail;
+    V.tail_smem = P.tail_smem;
+    int zc;
+    const dim3 gc = chunk_grid(d.nx, d.ny, d.nz, &zc);
+    V.chunk_g[0] = gc.x; V.chunk_g[1] = gc.y; V.chunk_g[2] = gc.z;
+    V.chunk_zc = zc;
+    V.dt_blocks = kDtBlocks;
+    V.st = st;
+    V.partials = partials;
+    V.dt = dt;
+    V.dtT = dtT;
+    V.omega = (T)d.mg_jacobi_omega;
+  }
+
   // ------------------------------------------------------------ entry points
   uf_status copy_in(T* dst, int lx, int ly, int lz, int pitch, const void* src) {
     if (!src) return fail(UF_ERR_ARG, "NULL buffer");
@@ -1341,6 +1519,18 @@ uf_status uf_adjoint_run(uf_grid* g, void* ws, size_t bytes, int nsteps, int ckp
                          double u_hi, double u_lo, void* dJ_dphi, double* J_out) {
   UF_NEED(g);
   return g->adjoint_run(ws, bytes, nsteps, ckpt_every, z_lo, z_hi, u_hi, u_lo, dJ_dphi, J_out);
+}
+uf_status uf_get_tuning(uf_grid* g, uf_tuning* out, int* levels) {
+  UF_NEED(g);
+  return g->get_tuning(out, levels);
+}
+uf_status uf_set_tuning(uf_grid* g, const uf_tuning* t) {
+  UF_NEED(g);
+  return g->set_tuning(t);
+}
+uf_status uf_autotune(uf_grid* g, int reps, uf_tuning* chosen, double* best_ms) {
+  UF_NEED(g);
+  return g->autotune(reps, chosen, best_ms);
 }
 uf_status uf_design_to_phi(uf_grid* g, int nbox, const double* boxes, const double* theta, double width, void* phi_out) {
   UF_NEED(g);

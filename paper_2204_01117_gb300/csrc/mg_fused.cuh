@@ -143,17 +143,19 @@ __device__ __forceinline__ int ring3(int k) { return ((k % 3) + 3) % 3; }
 __device__ __forceinline__ int ring4(int k) { return (k + 4) & 3; }
 
 template <typename T, int SM, bool CG>
-__global__ void __launch_bounds__(FT) k_mg_down(Level<T> F, Level<T> C, T omega, int zc, T* __restrict__ x,
-                                               const T* d0, const T* d1, const T* __restrict__ q,
-                                               double* partials, SolveState* st, cudaGraphConditionalHandle cond,
-                                               int use_cond) {
+__device__ __forceinline__ void mg_down_body(const Level<T>& F, const Level<T>& C, T omega, int zc, T* __restrict__ x,
+                                             const T* d0, const T* d1, const T* __restrict__ q, double* partials,
+                                             SolveState* st, cudaGraphConditionalHandle cond, int use_cond,
+                                             int* left, const VBlock& vb) {
   __shared__ T sQ[4][QP];
   __shared__ T sX[3][XP];
   __shared__ T sR[2][FT];
   __shared__ double sh[32];
   __shared__ bool last;
-  if (!CG && st->converged) return;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * zc;
+  // (a converged solve skips the whole cycle; in a batch, the instances
+  // that converged wait here for the others)
+  if (st->converged) return;
+  const int i0 = vb.x * TX, j0 = vb.y * TY, k0 = vb.z * zc;
   const int kend = min(F.nz, k0 + zc);
   const int tid = threadIdx.x, tx = tid & (TX - 1), ty = tid / TX;
   const int it0 = st->iter;
@@ -307,9 +309,9 @@ __global__ void __launch_bounds__(FT) k_mg_down(Level<T> F, Level<T> C, T omega,
     acc += dacc.value();
     acc = block_sum<FT>(acc, sh);
     const double vals[1] = {acc};
-    if (publish_partials<1>(partials, &st->ticket[3], vals, &last)) {
+    if (publish_partials<1>(partials, &st->ticket[3], vals, &last, vb)) {
       double tot[1];
-      reduce_partials_sum<FT, 1>(partials, tot, sh);
+      reduce_partials_sum<FT, 1>(partials, tot, sh, vb.n);
       if (tid == 0) {
         const double rr = tot[0];
         st->rr = rr;
@@ -326,12 +328,21 @@ __global__ void __launch_bounds__(FT) k_mg_down(Level<T> F, Level<T> C, T omega,
           if (st->sticky == 0) st->sticky = DEV_NOT_CONVERGED;
           st->converged = 1;
         }
-        if (st->converged && use_cond) cudaGraphSetConditional(cond, 0);
+        if (st->converged) signal_converged(cond, use_cond, left);
         st->ticket[3] = 0u;
       }
     }
   }
 }
+
+template <typename T, int SM, bool CG>
+__global__ void __launch_bounds__(FT) k_mg_down(Level<T> F, Level<T> C, T omega, int zc, T* __restrict__ x,
+                                               const T* d0, const T* d1, const T* __restrict__ q,
+                                               double* partials, SolveState* st, cudaGraphConditionalHandle cond,
+                                               int use_cond) {
+  mg_down_body<T, SM, CG>(F, C, omega, zc, x, d0, d1, q, partials, st, cond, use_cond, nullptr, vblock());
+}
+
 
 // -------------------------------------------------------------- up -------
 // Same z-march: t = x_pre + e(parent) on tile + halo 2 (ring of 4), first
@@ -339,14 +350,14 @@ __global__ void __launch_bounds__(FT) k_mg_down(Level<T> F, Level<T> C, T omega,
 // plane, written to `out` (F.t on coarse levels, z on the finest).
 // FINEST: also r.z and the CG beta.  Global loads run one plane ahead.
 template <typename T, int SM, bool FINEST>
-__global__ void __launch_bounds__(FT) k_mg_up(Level<T> F, Level<T> C, T omega, int zc, T* __restrict__ out, int mode,
-                                             double* partials, SolveState* st) {
+__device__ __forceinline__ void mg_up_body(const Level<T>& F, const Level<T>& C, T omega, int zc, T* __restrict__ out,
+                                           int mode, double* partials, SolveState* st, const VBlock& vb) {
   __shared__ T sT[4][QP];
   __shared__ T sU[3][XP];
   __shared__ double sh[32];
   __shared__ bool last;
   if (st->converged) return;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * zc;
+  const int i0 = vb.x * TX, j0 = vb.y * TY, k0 = vb.z * zc;
   const int kend = min(F.nz, k0 + zc);
   const int tid = threadIdx.x, tx = tid & (TX - 1), ty = tid / TX;
   const T* rcur = level_r(F, st->iter);
@@ -461,9 +472,9 @@ __global__ void __launch_bounds__(FT) k_mg_up(Level<T> F, Level<T> C, T omega, i
     acc += dacc.value();
     acc = block_sum<FT>(acc, sh);
     const double vals[1] = {acc};
-    if (publish_partials<1>(partials, &st->ticket[0], vals, &last)) {
+    if (publish_partials<1>(partials, &st->ticket[0], vals, &last, vb)) {
       double tot[1];
-      reduce_partials_sum<FT, 1>(partials, tot, sh);
+      reduce_partials_sum<FT, 1>(partials, tot, sh, vb.n);
       if (tid == 0) {
         finish_rz(st, tot[0], mode);
         st->ticket[0] = 0u;
@@ -471,6 +482,13 @@ __global__ void __launch_bounds__(FT) k_mg_up(Level<T> F, Level<T> C, T omega, i
     }
   }
 }
+
+template <typename T, int SM, bool FINEST>
+__global__ void __launch_bounds__(FT) k_mg_up(Level<T> F, Level<T> C, T omega, int zc, T* __restrict__ out, int mode,
+                                             double* partials, SolveState* st) {
+  mg_up_body<T, SM, FINEST>(F, C, omega, zc, out, mode, partials, st, vblock());
+}
+
 
 // ------------------------------------------------------------ tail -------
 // Levels lt..nl-1 live in shared memory, each as three arrays (r, a, u)
@@ -492,7 +510,7 @@ struct TailArgs {
 };
 
 template <typename T, int SM>
-__global__ void __launch_bounds__(TAIL_T) k_mg_tail(TailArgs<T> A, T omega, const SolveState* st) {
+__device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, T omega, const SolveState* st, const VBlock& vb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* S = reinterpret_cast<T*>(smem_raw);
   if (st->converged) return;
@@ -633,6 +651,12 @@ __global__ void __launch_bounds__(TAIL_T) k_mg_tail(TailArgs<T> A, T omega, cons
   }
 }
 
+template <typename T, int SM>
+__global__ void __launch_bounds__(TAIL_T) k_mg_tail(TailArgs<T> A, T omega, const SolveState* st) {
+  mg_tail_body<T, SM>(A, omega, st, vblock());
+}
+
+
 // ------------------------------------------- CG direction + SpMV --------
 // d = z (first iteration) or z + beta d_old, staged per z plane on the tile
 // plus a halo of 1 (ring of 4 planes, one barrier per plane, loads one plane
@@ -644,13 +668,13 @@ __global__ void __launch_bounds__(TAIL_T) k_mg_tail(TailArgs<T> A, T omega, cons
 // A Neumann neighbour takes d_c (its term is exactly zero); an outlet
 // neighbour is the staged zero ghost (term w d_c).
 template <typename T>
-__global__ void __launch_bounds__(FT) k_cg_dir_q(Level<T> L, int zc, const T* __restrict__ z, T* d0, T* d1,
-                                                T* __restrict__ q, double* partials, SolveState* st) {
+__device__ __forceinline__ void cg_dir_q_body(const Level<T>& L, int zc, const T* __restrict__ z, T* d0, T* d1,
+                                              T* __restrict__ q, double* partials, SolveState* st, const VBlock& vb) {
   __shared__ T sD[4][XP];
   __shared__ double sh[32];
   __shared__ bool last;
   if (st->converged) return;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * zc;
+  const int i0 = vb.x * TX, j0 = vb.y * TY, k0 = vb.z * zc;
   const int kend = min(L.nz, k0 + zc);
   const int tid = threadIdx.x, tx = tid & (TX - 1), ty = tid / TX;
   const int it = st->iter;
@@ -721,9 +745,9 @@ __global__ void __launch_bounds__(FT) k_cg_dir_q(Level<T> L, int zc, const T* __
   }
   double acc = block_sum<FT>(dacc.value(), sh);
   const double vals[1] = {acc};
-  if (publish_partials<1>(partials, &st->ticket[2], vals, &last)) {
+  if (publish_partials<1>(partials, &st->ticket[2], vals, &last, vb)) {
     double tot[1];
-    reduce_partials_sum<FT, 1>(partials, tot, sh);
+    reduce_partials_sum<FT, 1>(partials, tot, sh, vb.n);
     if (tid == 0) {
       st->dq = tot[0];
       st->alpha = st->rz / tot[0];
@@ -731,5 +755,12 @@ __global__ void __launch_bounds__(FT) k_cg_dir_q(Level<T> L, int zc, const T* __
     }
   }
 }
+
+template <typename T>
+__global__ void __launch_bounds__(FT) k_cg_dir_q(Level<T> L, int zc, const T* __restrict__ z, T* d0, T* d1,
+                                                T* __restrict__ q, double* partials, SolveState* st) {
+  cg_dir_q_body<T>(L, zc, z, d0, d1, q, partials, st, vblock());
+}
+
 
 }  // namespace uf

@@ -79,21 +79,34 @@ __device__ __forceinline__ T level_apply(const Level<T>& L, int i, int j, int k,
 }
 
 // Cell loop of a 32x8 thread tile over the z planes [z0, z1) of a block.
-#define UF_CELL_LOOP(L)                                                     \
-  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y; \
+#define UF_CELL_LOOP_VB(L, vb)                                              \
+  const int i = (vb).x * BX + threadIdx.x, j = (vb).y * BY + threadIdx.y;   \
   const bool inside = i < (L).nx && j < (L).ny;                             \
-  const int z0 = blockIdx.z * zc, z1 = min((L).nz, z0 + zc);
+  const int z0 = (vb).z * zc, z1 = min((L).nz, z0 + zc);
+#define UF_CELL_LOOP(L) UF_CELL_LOOP_VB(L, vblock())
+
+// Clears the WHILE condition of the graph that drives the CG loop once the
+// solve is done: at once for a single grid; for a batch, when the last of
+// its instances finishes (`left` counts the unfinished ones and each
+// instance decrements it exactly once).
+__device__ __forceinline__ void signal_converged(cudaGraphConditionalHandle cond, int use_cond, int* left) {
+  if (left) {
+    if (atomicSub(left, 1) == 1 && use_cond) cudaGraphSetConditional(cond, 0);
+  } else if (use_cond) {
+    cudaGraphSetConditional(cond, 0);
+  }
+}
 
 // ------------------------------------------------------------ CG kernels --
 
 // r = b - A x (warm start x = p^n).  A zero right-hand side gives x = 0.
 template <typename T>
-__global__ void __launch_bounds__(NT) k_cg_init(Level<T> L, const T* __restrict__ b, T* __restrict__ x, int zc,
-                                                double* partials, SolveState* st,
-                                                cudaGraphConditionalHandle cond, int use_cond) {
+__device__ __forceinline__ void cg_init_body(const Level<T>& L, const T* __restrict__ b, T* __restrict__ x, int zc,
+                                             double* partials, SolveState* st, cudaGraphConditionalHandle cond,
+                                             int use_cond, int* left, const VBlock& vb) {
   __shared__ double sh[32];
   __shared__ bool last;
-  UF_CELL_LOOP(L);
+  UF_CELL_LOOP_VB(L, vb);
   const bool zero_rhs = st->bb == 0.0;
   double acc = 0.0;
   DotAcc<T> dacc;
@@ -114,20 +127,28 @@ __global__ void __launch_bounds__(NT) k_cg_init(Level<T> L, const T* __restrict_
   acc += dacc.value();
   acc = block_sum<NT>(acc, sh);
   const double vals[1] = {acc};
-  if (publish_partials<1>(partials, &st->ticket[1], vals, &last)) {
+  if (publish_partials<1>(partials, &st->ticket[1], vals, &last, vb)) {
     double tot[1];
-    reduce_partials_sum<NT, 1>(partials, tot, sh);
+    reduce_partials_sum<NT, 1>(partials, tot, sh, vb.n);
     if (thread_linear_id() == 0) {
       st->rr = tot[0];
       st->rr0 = tot[0];
       if (zero_rhs || tot[0] <= st->tol2 * st->bb) {
         st->converged = 1;
-        if (use_cond) cudaGraphSetConditional(cond, 0);
+        signal_converged(cond, use_cond, left);
       }
       st->ticket[1] = 0u;
     }
   }
 }
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_cg_init(Level<T> L, const T* __restrict__ b, T* __restrict__ x, int zc,
+                                                double* partials, SolveState* st,
+                                                cudaGraphConditionalHandle cond, int use_cond) {
+  cg_init_body<T>(L, b, x, zc, partials, st, cond, use_cond, nullptr, vblock());
+}
+
 
 // d = z (first iteration) or z + beta d_old;  q = A d;  dq = d.q; alpha = rz/dq.
 // d ping-pongs between two buffers by iteration parity.
@@ -338,6 +359,26 @@ __global__ void __launch_bounds__(NT) k_solve_reset(Level<T> L, const T* __restr
       st->status = DEV_OK;
       st->ticket[0] = 0u;
     }
+  }
+}
+
+// Fixed right-hand side for timing solves: values in [-1, 1) from the
+// 32-bit finaliser of MurmurHash3 (A. Appleby) applied to the cell index.
+__device__ __forceinline__ unsigned int fmix32(unsigned int h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+template <typename T>
+__global__ void __launch_bounds__(NT) k_tune_rhs(Level<T> L, T* __restrict__ b, int zc) {
+  UF_CELL_LOOP(L);
+  if (!inside) return;
+  for (int k = z0; k < z1; ++k) {
+    const unsigned int id = (unsigned int)(i + L.nx * (j + L.ny * k));
+    b[lidx(L, i, j, k)] = T((double)fmix32(id * 2654435761u + 12345u) * (2.0 / 4294967296.0) - 1.0);
   }
 }
 

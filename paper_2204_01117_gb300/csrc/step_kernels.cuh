@@ -17,22 +17,21 @@ constexpr int BX = 32, BY = 8, NT = BX * BY;
 // dt = CFL h / max(|u|,|v|,|w|) over every face (all three lattices, padding
 // included: padding is zero).
 template <typename T>
-__global__ void __launch_bounds__(256) k_cfl_dt(const T* __restrict__ u, size_t nu, const T* __restrict__ v,
-                                                size_t nv, const T* __restrict__ w, size_t nw, double cfl_h,
-                                                double* partials, unsigned int* ticket, double* dt_out,
-                                                T* dtT_out) {
+__device__ __forceinline__ void cfl_dt_body(const T* __restrict__ u, size_t nu, const T* __restrict__ v, size_t nv,
+                                            const T* __restrict__ w, size_t nw, double cfl_h, double* partials,
+                                            unsigned int* ticket, double* dt_out, T* dtT_out, const VBlock& vb) {
   __shared__ double sh[32];
   __shared__ bool last;
   T mt = 0;   // max in the field type (exact), one conversion per thread
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)vb.n * blockDim.x;
+  const size_t t0 = vb.lin * (size_t)blockDim.x + threadIdx.x;
   for (size_t q = t0; q < nu; q += stride) mt = fmax(mt, fabs(u[q]));
   for (size_t q = t0; q < nv; q += stride) mt = fmax(mt, fabs(v[q]));
   for (size_t q = t0; q < nw; q += stride) mt = fmax(mt, fabs(w[q]));
   double m = block_max<256>((double)mt, sh);
   const double vals[1] = {m};
-  if (publish_partials<1>(partials, ticket, vals, &last)) {
-    const double mx = reduce_partials_max<256>(partials, sh);
+  if (publish_partials<1>(partials, ticket, vals, &last, vb)) {
+    const double mx = reduce_partials_max<256>(partials, sh, vb.n);
     if (threadIdx.x == 0) {
       if (mx > 0.0) {
         *dt_out = cfl_h / mx;
@@ -41,6 +40,14 @@ __global__ void __launch_bounds__(256) k_cfl_dt(const T* __restrict__ u, size_t 
       *ticket = 0u;
     }
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_cfl_dt(const T* __restrict__ u, size_t nu, const T* __restrict__ v,
+                                                size_t nv, const T* __restrict__ w, size_t nw, double cfl_h,
+                                                double* partials, unsigned int* ticket, double* dt_out,
+                                                T* dtT_out) {
+  cfl_dt_body<T>(u, nu, v, nv, w, nw, cfl_h, partials, ticket, dt_out, dtT_out, vblock());
 }
 
 // ----------------------------------------------- a1: strain + nu_t ------
@@ -85,16 +92,25 @@ __device__ __forceinline__ T limited_nut(const StepParams<T>& p, T kv, T omv, T 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT) k_eddy_viscosity(StepParams<T> p, const T* __restrict__ u,
-                                                       const T* __restrict__ v, const T* __restrict__ w,
-                                                       const T* __restrict__ kf, const T* __restrict__ om,
-                                                       T* __restrict__ nut) {
-  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+__device__ __forceinline__ void eddy_viscosity_body(const StepParams<T>& p, const T* __restrict__ u,
+                                                    const T* __restrict__ v, const T* __restrict__ w,
+                                                    const T* __restrict__ kf, const T* __restrict__ om,
+                                                    T* __restrict__ nut, const VBlock& vb) {
+  const int i = vb.x * BX + threadIdx.x, j = vb.y * BY + threadIdx.y, k = vb.z;
   if (i >= p.nx || j >= p.ny) return;
   const T dt = *p.dtT;
   const size_t c = idx_c(p, i, j, k);
   nut[c] = limited_nut(p, kf[c], om[c], strain_sq(u, v, w, p, i, j, k), dt);
 }
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_eddy_viscosity(StepParams<T> p, const T* __restrict__ u,
+                                                       const T* __restrict__ v, const T* __restrict__ w,
+                                                       const T* __restrict__ kf, const T* __restrict__ om,
+                                                       T* __restrict__ nut) {
+  eddy_viscosity_body<T>(p, u, v, w, kf, om, nut, vblock());
+}
+
 
 // ------------------------------------------------ a2: MacCormack advection
 struct Lattice {
@@ -184,11 +200,11 @@ __device__ __forceinline__ void plane_of(int bz, int nz, int& q, int& k) {
 
 // Forward semi-Lagrangian step phi^ = phi(x - dt u(x)) at every lattice point.
 template <typename T>
-__global__ void __launch_bounds__(NT) k_advect_forward(AdvectArgs<T> A) {
+__device__ __forceinline__ void advect_forward_body(const AdvectArgs<T>& A, const VBlock& vb) {
   int q, k;
-  plane_of(blockIdx.z, A.nz, q, k);
+  plane_of(vb.z, A.nz, q, k);
   const Lattice L = q == 0 ? A.Lu : (q == 1 ? A.Lv : A.Lw);
-  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  const int i = vb.x * BX + threadIdx.x, j = vb.y * BY + threadIdx.y;
   if (i >= L.Lx || j >= L.Ly) return;
   const T s = *A.dtT * A.inv_h;
   const T* F = q == 0 ? A.u : (q == 1 ? A.v : A.w);
@@ -199,15 +215,21 @@ __global__ void __launch_bounds__(NT) k_advect_forward(AdvectArgs<T> A) {
       sample<T, false>(F, L, T(i) - d[0], T(j) - d[1], T(k) - d[2]);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(NT) k_advect_forward(AdvectArgs<T> A) {
+  advect_forward_body<T>(A, vblock());
+}
+
+
 // Backward step, MacCormack correction and clamp on interior faces:
 // phi* = phi^ + (phi - phi^(x + dt u(x)))/2, clamped to the range of the 8
 // values of the forward sample (Selle et al. 2008).
 template <typename T>
-__global__ void __launch_bounds__(NT) k_advect_backward(AdvectArgs<T> A) {
+__device__ __forceinline__ void advect_backward_body(const AdvectArgs<T>& A, const VBlock& vb) {
   int q, k;
-  plane_of(blockIdx.z, A.nz, q, k);
+  plane_of(vb.z, A.nz, q, k);
   const Lattice L = q == 0 ? A.Lu : (q == 1 ? A.Lv : A.Lw);
-  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  const int i = vb.x * BX + threadIdx.x, j = vb.y * BY + threadIdx.y;
   if (i >= L.Lx || j >= L.Ly) return;
   const bool interior = q == 0 ? (i > 0 && i < A.nx) : (q == 1 ? (j > 0 && j < A.ny) : (k > 0 && k < A.nz));
   if (!interior) return;
@@ -225,17 +247,24 @@ __global__ void __launch_bounds__(NT) k_advect_backward(AdvectArgs<T> A) {
   Ft[id] = fmin(fmax(r, mn), mx);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(NT) k_advect_backward(AdvectArgs<T> A) {
+  advect_backward_body<T>(A, vblock());
+}
+
+
 // ------------------------------------------------- a3: diffusion ---------
 // Explicit (nu + nu_t) lap(u) on each face lattice; nu_t at a face is the
 // mean of its two cells.  Input boundary faces come from the BC rules, the
 // ghosts beyond tangential sides from the side's BC.  Writes interior faces.
 template <typename T>
-__global__ void __launch_bounds__(NT) k_diffuse(StepParams<T> p, const T* __restrict__ ui, const T* __restrict__ vi,
-                                                const T* __restrict__ wi, const T* __restrict__ nut,
-                                                T* __restrict__ uo, T* __restrict__ vo, T* __restrict__ wo) {
+__device__ __forceinline__ void diffuse_body(const StepParams<T>& p, const T* __restrict__ ui,
+                                             const T* __restrict__ vi, const T* __restrict__ wi,
+                                             const T* __restrict__ nut, T* __restrict__ uo, T* __restrict__ vo,
+                                             T* __restrict__ wo, const VBlock& vb) {
   int q, k;
-  plane_of(blockIdx.z, p.nz, q, k);
-  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  plane_of(vb.z, p.nz, q, k);
+  const int i = vb.x * BX + threadIdx.x, j = vb.y * BY + threadIdx.y;
   const T dt = *p.dtT;
   const T c = dt * p.inv_h * p.inv_h;
   const int nx = p.nx, ny = p.ny, nz = p.nz;
@@ -276,6 +305,14 @@ __global__ void __launch_bounds__(NT) k_diffuse(StepParams<T> p, const T* __rest
     wo[idx_c(p, i, j, k)] = x0 + c * (p.nu + nf) * lap;
   }
 }
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_diffuse(StepParams<T> p, const T* __restrict__ ui, const T* __restrict__ vi,
+                                                const T* __restrict__ wi, const T* __restrict__ nut,
+                                                T* __restrict__ uo, T* __restrict__ vo, T* __restrict__ wo) {
+  diffuse_body<T>(p, ui, vi, wi, nut, uo, vo, wo, vblock());
+}
+
 
 // ---------------------------------------------- a4 + a5: drag and BCs ----
 // Forward-Euler porosity drag u <- max(0, 1 - dt c U) u (Sec. 3) with c the
@@ -321,12 +358,13 @@ __device__ __forceinline__ T drag_w(const StepParams<T>& p, const T* __restrict_
 // Writes every face of the output: drag on interior faces; on boundary faces
 // the BC value, where an outlet face copies its (dragged) interior neighbour.
 template <typename T>
-__global__ void __launch_bounds__(NT) k_drag_bc(StepParams<T> p, const T* __restrict__ ui, const T* __restrict__ vi,
-                                                const T* __restrict__ wi, const T* __restrict__ cc,
-                                                T* __restrict__ uo, T* __restrict__ vo, T* __restrict__ wo) {
+__device__ __forceinline__ void drag_bc_body(const StepParams<T>& p, const T* __restrict__ ui,
+                                             const T* __restrict__ vi, const T* __restrict__ wi,
+                                             const T* __restrict__ cc, T* __restrict__ uo, T* __restrict__ vo,
+                                             T* __restrict__ wo, const VBlock& vb) {
   int q, k;
-  plane_of(blockIdx.z, p.nz, q, k);
-  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  plane_of(vb.z, p.nz, q, k);
+  const int i = vb.x * BX + threadIdx.x, j = vb.y * BY + threadIdx.y;
   const T dt = *p.dtT;
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   if (q == 0) {
@@ -349,6 +387,14 @@ __global__ void __launch_bounds__(NT) k_drag_bc(StepParams<T> p, const T* __rest
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(NT) k_drag_bc(StepParams<T> p, const T* __restrict__ ui, const T* __restrict__ vi,
+                                                const T* __restrict__ wi, const T* __restrict__ cc,
+                                                T* __restrict__ uo, T* __restrict__ vo, T* __restrict__ wo) {
+  drag_bc_body<T>(p, ui, vi, wi, cc, uo, vo, wo, vblock());
+}
+
+
 // ------------------------------------------- a6: pressure right-hand side
 // b = -(rho h / dt) (u(i+1)-u(i) + v(j+1)-v(j) + w(k+1)-w(k)), the
 // right-hand side of A p = b for the integer 7-point operator A.
@@ -368,13 +414,13 @@ struct SolveState {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(NT) k_pressure_rhs(StepParams<T> p, const T* __restrict__ u, const T* __restrict__ v,
-                                                     const T* __restrict__ w, T* __restrict__ b, int zc,
-                                                     double* partials, SolveState* st) {
+__device__ __forceinline__ void pressure_rhs_body(const StepParams<T>& p, const T* __restrict__ u,
+                                                  const T* __restrict__ v, const T* __restrict__ w, T* __restrict__ b,
+                                                  int zc, double* partials, SolveState* st, const VBlock& vb) {
   __shared__ double sh[32];
   __shared__ bool last;
-  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-  const int z0 = blockIdx.z * zc, z1 = min(p.nz, z0 + zc);
+  const int i = vb.x * BX + threadIdx.x, j = vb.y * BY + threadIdx.y;
+  const int z0 = vb.z * zc, z1 = min(p.nz, z0 + zc);
   double acc = 0.0;
   DotAcc<T> dacc;
   if (i < p.nx && j < p.ny) {
@@ -388,9 +434,9 @@ __global__ void __launch_bounds__(NT) k_pressure_rhs(StepParams<T> p, const T* _
   acc += dacc.value();
   acc = block_sum<NT>(acc, sh);
   const double vals[1] = {acc};
-  if (publish_partials<1>(partials, &st->ticket[0], vals, &last)) {
+  if (publish_partials<1>(partials, &st->ticket[0], vals, &last, vb)) {
     double tot[1];
-    reduce_partials_sum<NT, 1>(partials, tot, sh);
+    reduce_partials_sum<NT, 1>(partials, tot, sh, vb.n);
     if (thread_linear_id() == 0) {
       st->bb = tot[0];
       st->iter = 0;
@@ -401,15 +447,23 @@ __global__ void __launch_bounds__(NT) k_pressure_rhs(StepParams<T> p, const T* _
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(NT) k_pressure_rhs(StepParams<T> p, const T* __restrict__ u, const T* __restrict__ v,
+                                                     const T* __restrict__ w, T* __restrict__ b, int zc,
+                                                     double* partials, SolveState* st) {
+  pressure_rhs_body<T>(p, u, v, w, b, zc, partials, st, vblock());
+}
+
+
 // --------------------------------------------------------- a8: projection
 // u -= dt/(rho h) (p(c+) - p(c-)) on interior faces and on faces of outlet
 // sides (outer neighbour: the p = 0 ghost cell).  In place.
 template <typename T>
-__global__ void __launch_bounds__(NT) k_project(StepParams<T> p, const T* __restrict__ pr, T* __restrict__ u,
-                                                T* __restrict__ v, T* __restrict__ w) {
+__device__ __forceinline__ void project_body(const StepParams<T>& p, const T* __restrict__ pr, T* __restrict__ u,
+                                             T* __restrict__ v, T* __restrict__ w, const VBlock& vb) {
   int q, k;
-  plane_of(blockIdx.z, p.nz, q, k);
-  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  plane_of(vb.z, p.nz, q, k);
+  const int i = vb.x * BX + threadIdx.x, j = vb.y * BY + threadIdx.y;
   const T g = *p.dtT / (p.rho * p.h);
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   if (q == 0) {
@@ -432,6 +486,13 @@ __global__ void __launch_bounds__(NT) k_project(StepParams<T> p, const T* __rest
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(NT) k_project(StepParams<T> p, const T* __restrict__ pr, T* __restrict__ u,
+                                                T* __restrict__ v, T* __restrict__ w) {
+  project_body<T>(p, pr, u, v, w, vblock());
+}
+
+
 // ------------------------------------------------------- a9: k-omega -----
 // Forward Euler for k and omega after the projection (Sec. 3): first-order
 // upwind advection with the cell-centre velocity, 7-point diffusion with
@@ -440,10 +501,11 @@ __global__ void __launch_bounds__(NT) k_project(StepParams<T> p, const T* __rest
 // the projected velocity.  Ghosts: inlet values on inlet sides, zero
 // gradient elsewhere.  Floors k_min, omega_min.
 template <typename T>
-__global__ void __launch_bounds__(NT) k_turbulence(StepParams<T> p, const T* __restrict__ u, const T* __restrict__ v,
-                                                   const T* __restrict__ w, const T* __restrict__ ki,
-                                                   const T* __restrict__ oi, T* __restrict__ ko, T* __restrict__ oo) {
-  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+__device__ __forceinline__ void turbulence_body(const StepParams<T>& p, const T* __restrict__ u,
+                                                const T* __restrict__ v, const T* __restrict__ w,
+                                                const T* __restrict__ ki, const T* __restrict__ oi,
+                                                T* __restrict__ ko, T* __restrict__ oo, const VBlock& vb) {
+  const int i = vb.x * BX + threadIdx.x, j = vb.y * BY + threadIdx.y, k = vb.z;
   if (i >= p.nx || j >= p.ny) return;
   const T dt = *p.dtT;
   const size_t c = idx_c(p, i, j, k);
@@ -481,6 +543,14 @@ __global__ void __launch_bounds__(NT) k_turbulence(StepParams<T> p, const T* __r
   ko[c] = fmax(kc + dt * rk, p.k_min);
   oo[c] = fmax(oc + dt * ro, p.om_min);
 }
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_turbulence(StepParams<T> p, const T* __restrict__ u, const T* __restrict__ v,
+                                                   const T* __restrict__ w, const T* __restrict__ ki,
+                                                   const T* __restrict__ oi, T* __restrict__ ko, T* __restrict__ oo) {
+  turbulence_body<T>(p, u, v, w, ki, oi, ko, oo, vblock());
+}
+
 
 // ------------------------------------------------------ a10: objective ---
 // Sum over cells whose centre height lies in [z_lo, z_hi] of

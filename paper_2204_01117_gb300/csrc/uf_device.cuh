@@ -161,12 +161,25 @@ __device__ __forceinline__ int block_linear_id() {
 __device__ __forceinline__ int grid_blocks() { return gridDim.x * gridDim.y * gridDim.z; }
 __device__ __forceinline__ int thread_linear_id() { return threadIdx.x + blockDim.x * threadIdx.y; }
 
-// Publishes this block's partial(s) and returns true in the last block.
+// Coordinates of the block of work a kernel body processes: the launch's own
+// block (vblock()) for a single grid, or one item of a batch work list.
+// lin / n: linear index and count of the blocks that reduce into the same
+// partials buffer (one grid, or one instance of a batch).
+struct VBlock {
+  int x, y, z;
+  int lin, n;
+};
+__device__ __forceinline__ VBlock vblock() {
+  return VBlock{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, block_linear_id(), grid_blocks()};
+}
+
+// Publishes this block's partial(s) and returns true in the last of the vb.n
+// blocks that share the partials buffer and the ticket.
 template <int NV>
 __device__ __forceinline__ bool publish_partials(double* partials, unsigned int* ticket, const double* vals,
-                                                 bool* sh_last) {
+                                                 bool* sh_last, const VBlock& vb) {
   if (thread_linear_id() == 0) {
-    const int b = block_linear_id(), nb = grid_blocks();
+    const int b = vb.lin, nb = vb.n;
 #pragma unroll
     for (int q = 0; q < NV; ++q) partials[q * nb + b] = vals[q];
     __threadfence();
@@ -176,11 +189,15 @@ __device__ __forceinline__ bool publish_partials(double* partials, unsigned int*
   __syncthreads();
   return *sh_last;
 }
+template <int NV>
+__device__ __forceinline__ bool publish_partials(double* partials, unsigned int* ticket, const double* vals,
+                                                 bool* sh_last) {
+  return publish_partials<NV>(partials, ticket, vals, sh_last, vblock());
+}
 
 // In the last block: sum partials[q*nb ..] for q < NV in a fixed order.
 template <int NT, int NV>
-__device__ __forceinline__ void reduce_partials_sum(const double* partials, double* out, double* sh) {
-  const int nb = grid_blocks();
+__device__ __forceinline__ void reduce_partials_sum(const double* partials, double* out, double* sh, int nb) {
   for (int q = 0; q < NV; ++q) {
     double s = 0.0;
     for (int b = thread_linear_id(); b < nb; b += NT) s += __ldcg(partials + q * nb + b);
@@ -188,9 +205,12 @@ __device__ __forceinline__ void reduce_partials_sum(const double* partials, doub
     if (thread_linear_id() == 0) out[q] = s;
   }
 }
+template <int NT, int NV>
+__device__ __forceinline__ void reduce_partials_sum(const double* partials, double* out, double* sh) {
+  reduce_partials_sum<NT, NV>(partials, out, sh, grid_blocks());
+}
 template <int NT>
-__device__ __forceinline__ double reduce_partials_max(const double* partials, double* sh) {
-  const int nb = grid_blocks();
+__device__ __forceinline__ double reduce_partials_max(const double* partials, double* sh, int nb) {
   double s = 0.0;
   for (int b = thread_linear_id(); b < nb; b += NT) s = fmax(s, __ldcg(partials + b));
   return block_max<NT>(s, sh);

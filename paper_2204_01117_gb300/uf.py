@@ -20,7 +20,7 @@ ROOT = os.path.dirname(_HERE)
 CSRC = os.path.join(_HERE, "csrc")
 LIB_PATH = os.path.join(_HERE, "_build", "libuf.so")
 HEADER = os.path.join(ROOT, "include", "uf.h")
-SOURCES = ["capi.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "noalloc.cu", "batch.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo",
               "--expt-extended-lambda", "-Xcompiler", "-fPIC", "-shared"]
 
@@ -57,6 +57,16 @@ class StepStats(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("cg_iters", ctypes.c_int),
                 ("cg_rel_residual", ctypes.c_double), ("status", ctypes.c_int),
                 ("cg_iters_total", ctypes.c_longlong)]
+
+
+MAX_LEVELS = 16
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("tail_level", ctypes.c_int), ("march_zc", ctypes.c_int * MAX_LEVELS)]
+
+    def as_dict(self) -> dict:
+        return {"tail_level": self.tail_level, "march_zc": list(self.march_zc)}
 
 
 class KernelTime(ctypes.Structure):
@@ -154,6 +164,26 @@ def load():
     lib.uf_design_vjp.restype = ip
     lib.uf_poisson_solve_static.argtypes = [ip, ip, ip, dp, vp, vp, dp, ip, vp, P(ip), P(dp)]
     lib.uf_poisson_solve_static.restype = ip
+    lib.uf_get_tuning.argtypes = [vp, P(Tuning), P(ip)]
+    lib.uf_get_tuning.restype = ip
+    lib.uf_set_tuning.argtypes = [vp, P(Tuning)]
+    lib.uf_set_tuning.restype = ip
+    lib.uf_autotune.argtypes = [vp, ip, P(Tuning), P(dp)]
+    lib.uf_autotune.restype = ip
+    lib.uf_batch_workspace_bytes.argtypes = [ip, P(GridDesc)]
+    lib.uf_batch_workspace_bytes.restype = ctypes.c_size_t
+    lib.uf_batch_create.argtypes = [ip, P(GridDesc), vp, ctypes.c_size_t, vp, P(vp)]
+    lib.uf_batch_create.restype = ip
+    lib.uf_batch_grid.argtypes = [vp, ip, P(vp)]
+    lib.uf_batch_grid.restype = ip
+    lib.uf_batch_run.argtypes = [vp, ip, P(StepStats)]
+    lib.uf_batch_run.restype = ip
+    lib.uf_batch_launch_counts.argtypes = [vp, P(ip), P(ip)]
+    lib.uf_batch_launch_counts.restype = ip
+    lib.uf_batch_autotune.argtypes = [vp, ip, P(ip)]
+    lib.uf_batch_autotune.restype = ip
+    lib.uf_batch_destroy.argtypes = [vp]
+    lib.uf_batch_destroy.restype = ip
     for name in ("uf_create_grid", "uf_destroy", "uf_set_porosity", "uf_set_state", "uf_get_state",
                  "uf_init_state", "uf_step", "uf_run", "uf_objective", "uf_divergence",
                  "uf_apply_poisson", "uf_poisson_solve"):
@@ -260,14 +290,38 @@ class Grid:
         check(self.lib.uf_create_grid(ctypes.byref(self.desc), ctypes.c_void_p(self.workspace.data_ptr()),
                                       nbytes, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
         self._h = h
+        self._owned = True
+        self._init_shapes(nx, ny, nz)
+
+    def _init_shapes(self, nx, ny, nz):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.shapes = {"u": (nz, ny, nx + 1), "v": (nz, ny + 1, nx), "w": (nz + 1, ny, nx),
                        "p": (nz, ny, nx), "k": (nz, ny, nx), "omega": (nz, ny, nx),
                        "phi": (nz, ny, nx), "nut": (nz, ny, nx)}
 
+    @classmethod
+    def _borrowed(cls, owner, handle, desc: GridDesc, stream):
+        """A grid whose handle belongs to `owner` (a Batch): never destroyed here."""
+        import torch
+        g = cls.__new__(cls)
+        g.lib = load()
+        g.desc = desc
+        if desc.precision == F64:
+            g.torch_dtype, g.np_dtype = torch.float64, np.float64
+        else:
+            g.torch_dtype, g.np_dtype = torch.float32, np.float32
+        g.workspace = None
+        g.stream = stream
+        g._h = handle
+        g._owned = False
+        g._owner = owner
+        g._init_shapes(desc.nx, desc.ny, desc.nz)
+        return g
+
     def close(self):
         if getattr(self, "_h", None):
-            self.lib.uf_destroy(self._h)
+            if getattr(self, "_owned", True):
+                self.lib.uf_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -415,6 +469,29 @@ class Grid:
         check(self.lib.uf_design_vjp(self._h, b.shape[0], dptr(b), dptr(t), width, lp, dptr(g)))
         return g
 
+    # -- launch tuning ----------------------------------------------------
+    def get_tuning(self):
+        """(tuning dict with resolved values, number of MG levels)."""
+        t = Tuning()
+        n = ctypes.c_int()
+        check(self.lib.uf_get_tuning(self._h, ctypes.byref(t), ctypes.byref(n)))
+        return t.as_dict(), n.value
+
+    def set_tuning(self, tail_level: int = 0, march_zc=None) -> None:
+        """0 / None: automatic.  march_zc: per-level z planes per block."""
+        t = Tuning()
+        t.tail_level = tail_level
+        for l, z in enumerate(march_zc or []):
+            t.march_zc[l] = z
+        check(self.lib.uf_set_tuning(self._h, ctypes.byref(t)))
+
+    def autotune(self, reps: int = 5):
+        """Times the candidate tunings, keeps the fastest: (tuning, ms per solve)."""
+        t = Tuning()
+        ms = ctypes.c_double()
+        check(self.lib.uf_autotune(self._h, reps, ctypes.byref(t), ctypes.byref(ms)))
+        return t.as_dict(), ms.value
+
     def launch_counts(self):
         """(kernels per step outside the CG loop, kernels per CG iteration)."""
         fixed = ctypes.c_int()
@@ -431,6 +508,76 @@ class Grid:
     def set_fields(self, st: dict) -> None:
         for n, val in st.items():
             self.set_state(n, val if _is_tensor(val) else np.asarray(val, dtype=self.np_dtype))
+
+
+class Batch:
+    """Many grids advanced together by batched persistent launches under one
+    CUDA graph (include/uf.h, "Batched execution").  `instances` is a list of
+    dicts of grid parameters (nx, ny, nz and any uf_grid_desc field); all
+    share `precision`.  batch.grids[i] is a Grid handle of instance i owned
+    by the batch."""
+
+    def __init__(self, instances, precision: str = "f32", stream=None):
+        import torch
+        self.lib = load()
+        n = len(instances)
+        descs = (GridDesc * n)()
+        for i, p in enumerate(instances):
+            descs[i] = default_desc(precision=precision, **p)
+        self.descs = descs
+        nbytes = int(self.lib.uf_batch_workspace_bytes(n, descs))
+        if nbytes == 0:
+            raise UFError(UF_ERR_ARG, last_error())
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        h = ctypes.c_void_p()
+        check(self.lib.uf_batch_create(n, descs, ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                       ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self._h = h
+        self.n = n
+        self.grids = []
+        for i in range(n):
+            gh = ctypes.c_void_p()
+            check(self.lib.uf_batch_grid(h, i, ctypes.byref(gh)))
+            self.grids.append(Grid._borrowed(self, gh, descs[i], self.stream))
+
+    def run(self, nsteps: int, stats: bool = True):
+        """nsteps batched steps; per-instance StepStats after the last one."""
+        if not stats:
+            check(self.lib.uf_batch_run(self._h, nsteps, None))
+            return None
+        arr = (StepStats * self.n)()
+        check(self.lib.uf_batch_run(self._h, nsteps, arr))
+        return list(arr)
+
+    def launch_counts(self):
+        fixed = ctypes.c_int()
+        per = ctypes.c_int()
+        check(self.lib.uf_batch_launch_counts(self._h, ctypes.byref(fixed), ctypes.byref(per)))
+        return fixed.value, per.value
+
+    def autotune(self, reps: int = 5) -> int:
+        """Per size class autotuning; returns the number of classes."""
+        c = ctypes.c_int()
+        check(self.lib.uf_batch_autotune(self._h, reps, ctypes.byref(c)))
+        return c.value
+
+    @property
+    def cells(self) -> int:
+        return sum(d.nx * d.ny * d.nz for d in self.descs)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for g in self.grids:
+                g._h = None
+            self.lib.uf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _make_functions():

@@ -59,3 +59,55 @@ def test_null_arguments_are_errors(lib):
     assert lib.uf_step(None, None) == uf.UF_ERR_ARG
     assert lib.uf_destroy(None) == uf.UF_ERR_ARG
     assert lib.uf_last_step_launches(None) == 0
+
+
+def _descs(*params, precision="f32"):
+    arr = (uf.GridDesc * len(params))()
+    for i, p in enumerate(params):
+        arr[i] = uf.default_desc(precision=precision, **p)
+    return arr
+
+
+def test_batch_workspace_is_sum_of_grids_plus_tables(lib):
+    params = [dict(nx=96, ny=96, nz=32), dict(nx=128, ny=64, nz=40, wind_dir_deg=135.0), dict(nx=33, ny=45, nz=9)]
+    descs = _descs(*params)
+    total = lib.uf_batch_workspace_bytes(len(params), descs)
+    grids = sum(uf.workspace_bytes(descs[i]) for i in range(len(params)))
+    assert grids < total < grids + len(params) * 256 + 64 * 1024 + 4096 * len(params) + 200 * 1024
+
+
+@pytest.mark.parametrize("case,msg", [
+    ("empty", "batch size"), ("too_many", "batch size"), ("mixed_precision", "precision"),
+    ("not_mg", "MG preconditioner"), ("mixed_smoother", "smoother"), ("bad_instance", "instance 1"),
+])
+def test_batch_descriptions_rejected_on_host(lib, case, msg):
+    base = dict(nx=32, ny=16, nz=8)
+    if case == "empty":
+        n, descs = 0, _descs(base)
+    elif case == "too_many":
+        n, descs = 65, _descs(*([base] * 65))
+    elif case == "mixed_precision":
+        descs = _descs(base, base)
+        descs[1] = uf.default_desc(precision="f64", **base)
+        n = 2
+    elif case == "not_mg":
+        n, descs = 2, _descs(base, dict(base, precond=uf.PRECOND["ai1"]))
+    elif case == "mixed_smoother":
+        n, descs = 2, _descs(base, dict(base, mg_smoother=uf.SMOOTHER["rbgs"]))
+    else:
+        n, descs = 2, _descs(base, dict(base, nx=1))
+    assert lib.uf_batch_workspace_bytes(n, descs) == 0
+    assert msg in uf.last_error()
+
+
+def test_batch_null_arguments_are_errors(lib):
+    descs = _descs(dict(nx=32, ny=16, nz=8))
+    h = ctypes.c_void_p()
+    assert lib.uf_batch_create(1, descs, None, 0, None, ctypes.byref(h)) == uf.UF_ERR_ARG
+    assert lib.uf_batch_create(1, descs, ctypes.c_void_p(256), 16, None, ctypes.byref(h)) == uf.UF_ERR_NOMEM
+    assert lib.uf_batch_run(None, 1, None) == uf.UF_ERR_ARG
+    assert lib.uf_batch_grid(None, 0, ctypes.byref(h)) == uf.UF_ERR_ARG
+    assert lib.uf_batch_autotune(None, 1, None) == uf.UF_ERR_ARG
+    assert lib.uf_get_tuning(None, None, None) == uf.UF_ERR_ARG
+    assert lib.uf_set_tuning(None, None) == uf.UF_ERR_ARG
+    assert lib.uf_autotune(None, 1, None, None) == uf.UF_ERR_ARG
