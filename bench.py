@@ -12,7 +12,10 @@ needed between steps.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 The line also carries "adjoint": the adjoint/forward time ratio on the
-128 x 128 x 48 parametric design workload (see adjoint_leg).
+128 x 128 x 48 parametric design workload (see adjoint_leg), and "batched":
+32 instances of uneven size and wind direction advanced by the batched
+persistent launches, against the same instances stepped one after another
+(see batched_leg).
 
 Multi-GPU: replicas only (each rank advances its own independent grid; no
 collective in the data path), weak scaling; rank 0 prints one JSON line.
@@ -205,6 +208,88 @@ def adjoint_leg():
     return out
 
 
+# ---------------------------------------------------------------- batched leg
+
+def batched_leg(steps: int = 10, peak: float = 6790.0, peak_kind: str = "measured"):
+    """Batched vs sequential single-grid throughput on 32 instances of uneven
+    size (nx, ny in 96..256, nz in 32..64), seeded urban layouts scaled by
+    area, wind direction uniform in [0, 360) and speed in [2, 8] m/s, FP32.
+    The batch is autotuned per size class first; the sequential run is the
+    plain single-grid step of each instance in turn (default tuning) on one
+    stream.  Both are timed with CUDA events over `steps` steps after 3
+    warm-up steps; the roofline comes from one eagerly launched batched step
+    (per-launch CUDA events)."""
+    import numpy as np
+    import torch
+    from paper_2204_01117_gb300 import layouts, uf
+    insts = layouts.batch_instances(32, seed=0)
+    params = [dict(nx=sc.nx, ny=sc.ny, nz=sc.nz, **sc.params()) for sc in insts]
+    b = uf.Batch(params, precision="f32")
+    for sc, g in zip(insts, b.grids):
+        g.set_porosity(sc.phi.astype(np.float32))
+        g.init_state()
+    classes = b.autotune(reps=2)
+    cells = b.cells
+
+    def timed(stream, fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    b.run(3, stats=False)
+    ms_b = timed(b.stream, lambda: b.run(steps, stats=False))
+    st = b.run(1)
+    fixed, per_iter = b.launch_counts()
+    prof = b.profile_step()
+    dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
+    avg_ms = dom["total_ms"] / dom["launches"]
+    achieved = dom["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
+    total_prof = sum(k["total_ms"] for k in prof.values())
+    b.close()
+    del b
+    torch.cuda.empty_cache()
+
+    s = torch.cuda.Stream()
+    solos = []
+    for sc, p in zip(insts, params):
+        q = dict(p)
+        nx, ny, nz = q.pop("nx"), q.pop("ny"), q.pop("nz")
+        g = uf.Grid(nx, ny, nz, precision="f32", stream=s, **q)
+        g.set_porosity(sc.phi.astype(np.float32))
+        g.init_state()
+        g.run(3, stats=False)
+        solos.append(g)
+
+    def run_solos():
+        for g in solos:
+            g.run(steps, stats=False)
+
+    ms_s = timed(s, run_solos)
+    for g in solos:
+        g.close()
+    del solos
+    torch.cuda.empty_cache()
+    return {
+        "workload": "32 instances, nx, ny in 96..256 (multiples of 16), nz in 32..64 (multiples of 8), "
+                    "seeded urban layouts scaled by area, wind direction U[0,360) deg, speed U[2,8] m/s, FP32 "
+                    "fields + FP64 reductions; 300-step runs, timed over " + str(steps) + " steps",
+        "instances": len(insts), "cells": cells, "size_classes": classes,
+        "batched": {"value": cells * steps / (ms_b * 1e-3), "unit": UNIT, "ms_per_step": ms_b / steps,
+                    "cg_iters_min_max": [min(x.cg_iters for x in st), max(x.cg_iters for x in st)],
+                    "launches_fixed_per_iter": [fixed, per_iter]},
+        "sequential_single_grid": {"value": cells * steps / (ms_s * 1e-3), "unit": UNIT, "ms_per_step": ms_s / steps},
+        "speedup": ms_s / ms_b,
+        "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
+                     "kernel_share_of_step": dom["total_ms"] / total_prof,
+                     "bytes_per_launch": dom["bytes_per_launch"], "avg_launch_us": avg_ms * 1e3},
+    }
+
+
 # ---------------------------------------------------------------- oracle arm
 
 def oracle_sample(max_seconds: float = 150.0, steps_wanted: int = 1):
@@ -359,6 +444,8 @@ def run_ours(args):
     }
     if not args.no_adjoint:
         line["adjoint"] = adjoint_leg()
+    if not args.no_batched:
+        line["batched"] = batched_leg(peak=peak, peak_kind=peak_kind)
     if not args.no_cpu_baseline and world == 1:
         rate, cores, sample, done, dt = oracle_sample(max_seconds=60.0, steps_wanted=1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
@@ -377,6 +464,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing leg")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched 32-instance leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -319,9 +319,17 @@ uf_status uf_batch_run(uf_batch* b, int nsteps, uf_step_stats* stats);
  * *per_iter per CG iteration of the slowest instance. */
 uf_status uf_batch_launch_counts(uf_batch* b, int* fixed, int* per_iter);
 
-/* Autotunes per size class: instances whose grids have the same multigrid
- * hierarchy shape share one tuning, chosen by uf_autotune on the first of
- * them; the batch graphs are rebuilt.  classes: number of size classes
+/* One batched step launched eagerly (no graph), each launch bracketed by
+ * CUDA events on the batch's stream; the host polls the unfinished-instance
+ * count before every CG iteration.  Fills per-kernel aggregates as
+ * uf_profile_step does (names prefixed "b_"; bytes_per_launch summed over
+ * the instances of the launch).  Advances every instance by one step. */
+uf_status uf_batch_profile_step(uf_batch* b, uf_kernel_time* out, int capacity, int* count);
+
+/* Autotunes per size class: instances with the same number of multigrid
+ * levels and cell counts within a factor sqrt(2) (one half-octave bin) share
+ * one tuning, chosen by uf_autotune on the first of them; the batch graphs
+ * are rebuilt.  classes: number of size classes
  * (may be NULL). */
 uf_status uf_batch_autotune(uf_batch* b, int reps, int* classes);
 

@@ -182,6 +182,8 @@ def load():
     lib.uf_batch_launch_counts.restype = ip
     lib.uf_batch_autotune.argtypes = [vp, ip, P(ip)]
     lib.uf_batch_autotune.restype = ip
+    lib.uf_batch_profile_step.argtypes = [vp, P(KernelTime), ip, P(ip)]
+    lib.uf_batch_profile_step.restype = ip
     lib.uf_batch_destroy.argtypes = [vp]
     lib.uf_batch_destroy.restype = ip
     for name in ("uf_create_grid", "uf_destroy", "uf_set_porosity", "uf_set_state", "uf_get_state",
@@ -555,6 +557,18 @@ class Batch:
         per = ctypes.c_int()
         check(self.lib.uf_batch_launch_counts(self._h, ctypes.byref(fixed), ctypes.byref(per)))
         return fixed.value, per.value
+
+    def profile_step(self, capacity: int = 96):
+        """One eager batched step with per-launch CUDA events:
+        {kernel name: dict(launches, total_ms, bytes_per_launch)}."""
+        arr = (KernelTime * capacity)()
+        n = ctypes.c_int()
+        check(self.lib.uf_batch_profile_step(self._h, arr, capacity, ctypes.byref(n)))
+        out = {}
+        for i in range(min(n.value, capacity)):
+            k = arr[i]
+            out[k.name.decode()] = dict(launches=k.launches, total_ms=k.total_ms, bytes_per_launch=k.bytes_per_launch)
+        return out
 
     def autotune(self, reps: int = 5) -> int:
         """Per size class autotuning; returns the number of classes."""
