@@ -60,6 +60,28 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_scalar(x: float, op: str) -> float:
+    """All-reduce of one number over the ranks of the default process group
+    ("max" or "sum"); the identity without one.  The tensor lives on the GPU
+    for NCCL and on the host for gloo."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def weak_scaling_rate(cells_local: float, steps: int, seconds_local: float):
+    """Replicas: each rank advances its own grid.  Whole-job rate = cells of
+    all ranks x steps / the slowest rank's time.  Returns (rate, slowest)."""
+    cells = reduce_scalar(float(cells_local), "sum")
+    slowest = reduce_scalar(float(seconds_local), "max")
+    return cells * steps / slowest, slowest
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -380,11 +402,8 @@ def run_ours(args):
     st1 = g.step()
     iters_timed = st1.cg_iters_total - st0.cg_iters_total - st1.cg_iters
     launches = args.steps * fixed + iters_timed * per_iter
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    value = sc.cells * args.steps * world / (ms * 1e-3)
+    value, slowest_s = weak_scaling_rate(sc.cells, args.steps, ms * 1e-3)
+    ms = slowest_s * 1e3
 
     # -- end to end through the C ABI with pinned host buffers ------------
     names = ("u", "v", "w", "p", "k", "omega")
@@ -404,12 +423,7 @@ def run_ours(args):
         for n in names:
             g.get_state(n, out=host_out[n])
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if pg:
-        t = torch.tensor([e2e_s], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = sc.cells * e2e_steps * world / e2e_s
+    e2e_value, e2e_s = weak_scaling_rate(sc.cells, e2e_steps, time.perf_counter() - t0)
 
     # -- per-kernel CUDA-event timing of one eagerly launched step ----------
     pst, kernels = g.profile_step()
