@@ -235,6 +235,18 @@ size_t uf_adjoint_workspace_bytes(uf_grid* g, int nsteps, int ckpt_every);
 uf_status uf_adjoint_run(uf_grid* g, void* d_ws, size_t bytes, int nsteps, int ckpt_every, double z_lo, double z_hi,
                          double u_hi, double u_lo, void* dJ_dphi, double* J_out);
 
+/* Vector-Jacobian product of one step (uf_step with the grid's fixed dt) at
+ * the grid's current state X: given lam_out, the cotangent of the step's
+ * output state, fills lam_in = (dX'/dX)^T lam_out and, if lam_phi is not
+ * NULL, lam_phi = (dX'/dphi)^T lam_out.  lam_out and lam_in are arrays of
+ * five dense field buffers in the order u, v, w, k, omega (grid precision,
+ * host or device); the pressure is not an input (it only warm-starts the
+ * solve).  The grid's state is restored afterwards.  d_ws: device workspace
+ * of at least uf_adjoint_workspace_bytes(g, 1, 1) bytes.  Synchronises.
+ * Errors as uf_adjoint_run. */
+uf_status uf_step_vjp(uf_grid* g, void* d_ws, size_t bytes, const void* const* lam_out, void* const* lam_in,
+                      void* lam_phi);
+
 /* Parametric design -> porosity (smoothed cut-cell idea of Sec. 3, "Urban
  * model resolving"): nbox (<= 64) boxes with base footprints
  * boxes[4i..4i+3] = (x_a, x_b, y_a, y_b) [m] and parameters

@@ -806,6 +806,111 @@ class GridImpl final : public uf_grid {
   T* adj_mu = nullptr;
   T* adj_b = nullptr;
 
+  // Adjoint arrays inside the workspace (after the tapes and checkpoints).
+  struct AdjArrays {
+    FaceSet L0, L1, Lt, L2, Lh;   // adjoints: step input, step output, advected, diffused, forward SL
+    T *lk0, *lk1, *lo0, *lo1, *lnut, *lc, *mu, *badj, *lphi;
+  };
+  AdjArrays adj_arrays(T* base, const AdjLayout& A) const {
+    AdjArrays R;
+    T* lam = base + A.lam;
+    R.L0 = faces_at(lam);
+    R.L1 = faces_at(lam + A.faceN);
+    R.Lt = faces_at(lam + 2 * A.faceN);
+    R.L2 = faces_at(lam + 3 * A.faceN);
+    R.Lh = faces_at(lam + 4 * A.faceN);
+    T* cells = lam + 5 * A.faceN;
+    R.lk0 = cells; R.lk1 = cells + A.cellN; R.lo0 = cells + 2 * A.cellN; R.lo1 = cells + 3 * A.cellN;
+    R.lnut = cells + 4 * A.cellN; R.lc = cells + 5 * A.cellN; R.mu = cells + 6 * A.cellN;
+    R.badj = cells + 7 * A.cellN; R.lphi = cells + 8 * A.cellN;
+    return R;
+  }
+
+  // The adjoint pressure solve: the step's MG-PCG captured with (badj -> mu)
+  // in place of (b -> p).
+  uf_status ensure_adj_solve(T* mu, T* badj) {
+    if (adj_solve_exec && adj_mu == mu && adj_b == badj) return UF_OK;
+    if (adj_solve_exec) cudaGraphExecDestroy(adj_solve_exec);
+    adj_solve_exec = nullptr;
+    sol_x = mu;
+    sol_b = badj;
+    int nf, ns, ni;
+    auto pre = [&](cudaStream_t s2) {
+      int zc;
+      dim3 g = chunk_grid(d.nx, d.ny, d.nz, &zc);
+      uf::k_solve_reset<T><<<g, dim3(uf::BX, uf::BY), 0, s2>>>(lv[0], badj, zc, partials, st);
+      rec_count++;
+    };
+    uf_status s = capture(&adj_solve_exec, pre, [&](cudaStream_t) {}, &nf, &ns, &ni);
+    sol_x = p;
+    sol_b = b;
+    if (s != UF_OK) return s;
+    adj_mu = mu;
+    adj_b = badj;
+    return UF_OK;
+  }
+
+  // Runs one step from the current state and tapes it into slot t.
+  uf_status tape_step(T* t, const AdjLayout& A) {
+    UF_CUDA(save_state(t, A));
+    UF_CUDA(cudaGraphLaunch(step_exec[parity], stream));
+    parity ^= 1;
+    UF_CUDA(copy_cell(t + A.s_nut, nut));
+    UF_CUDA(copy_faces(faces_at(t + A.s_uh), uh, vh, wh));
+    UF_CUDA(copy_faces(faces_at(t + A.s_ut), ut, vt, wt));
+    UF_CUDA(copy_faces(faces_at(t + A.s_u2), u2, v2, w2));
+    UF_CUDA(copy_faces(faces_at(t + A.s_u1), u, v, w));
+    return UF_OK;
+  }
+
+  // Transpose of the taped step in slot t: from the adjoint of its output
+  // (R.L1, R.lk1, R.lo1) to the adjoint of its input (R.L0, R.lk0, R.lo0);
+  // dJ/dc accumulates in R.lc.
+  uf_status reverse_step(const T* t, const AdjLayout& A, const AdjArrays& R) {
+    const size_t faceB = A.faceN * sizeof(T), cellB = A.cellN * sizeof(T);
+    const dim3 blk(uf::BX, uf::BY);
+    const dim3 gc = plane_grid(d.nx, d.ny, d.nz);
+    const dim3 ga = plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1);
+    const FaceSet U0 = faces_at(const_cast<T*>(t));
+    const T* K0 = t + A.faceN;
+    const T* O0 = t + A.faceN + A.cellN;
+    const T* NUT = t + A.s_nut;
+    const FaceSet UH = faces_at(const_cast<T*>(t) + A.s_uh);
+    const FaceSet UT = faces_at(const_cast<T*>(t) + A.s_ut);
+    const FaceSet U2 = faces_at(const_cast<T*>(t) + A.s_u2);
+    const FaceSet U1 = faces_at(const_cast<T*>(t) + A.s_u1);
+    UF_CUDA(cudaMemsetAsync(R.L0.u, 0, faceB, stream));
+    UF_CUDA(cudaMemsetAsync(R.Lt.u, 0, 3 * faceB, stream));   // Lt, L2, Lh are contiguous
+    UF_CUDA(cudaMemsetAsync(R.lk0, 0, cellB, stream));
+    UF_CUDA(cudaMemsetAsync(R.lo0, 0, cellB, stream));
+    UF_CUDA(cudaMemsetAsync(R.lnut, 0, cellB, stream));
+    // a9^T: k-omega update
+    uf::k_turbulence_adj<T><<<gc, blk, 0, stream>>>(sp, U1.u, U1.v, U1.w, K0, O0, R.lk1, R.lo1, R.lk0, R.lo0, R.L1.u,
+                                                    R.L1.v, R.L1.w);
+    // a8^T: projection (A symmetric: the same MG-PCG)
+    uf::k_proj_adj_rhs<T><<<gc, blk, 0, stream>>>(sp, R.L1.u, R.L1.v, R.L1.w, R.badj);
+    UF_CUDA(cudaGraphLaunch(adj_solve_exec, stream));
+    uf::k_proj_adj_apply<T><<<ga, blk, 0, stream>>>(sp, R.mu, R.L1.u, R.L1.v, R.L1.w);
+    // a4/a5^T: drag and velocity BCs
+    uf::k_drag_bc_adj<T><<<ga, blk, 0, stream>>>(sp, U2.u, U2.v, U2.w, cc, R.L1.u, R.L1.v, R.L1.w, R.L2.u, R.L2.v,
+                                                 R.L2.w, R.lc);
+    // a3^T: diffusion
+    uf::k_diffuse_adj<T><<<ga, blk, 0, stream>>>(sp, UT.u, UT.v, UT.w, NUT, R.L2.u, R.L2.v, R.L2.w, R.Lt.u, R.Lt.v,
+                                                 R.Lt.w, R.lnut);
+    // a2^T: MacCormack advection
+    uf::AdvectArgs<T> Aa = advect_args();
+    Aa.u = U0.u; Aa.v = U0.v; Aa.w = U0.w;
+    Aa.uh = UH.u; Aa.vh = UH.v; Aa.wh = UH.w;
+    uf::AdvectAdj<T> Ja{R.Lt.u, R.Lt.v, R.Lt.w, R.Lh.u, R.Lh.v, R.Lh.w, R.L0.u, R.L0.v, R.L0.w};
+    uf::k_advect_backward_adj<T><<<ga, blk, 0, stream>>>(Aa, Ja);
+    uf::k_advect_forward_adj<T><<<ga, blk, 0, stream>>>(Aa, Ja);
+    // a1^T: eddy viscosity
+    uf::k_eddy_viscosity_adj<T><<<gc, blk, 0, stream>>>(sp, U0.u, U0.v, U0.w, K0, O0, R.lnut, R.lk0, R.lo0, R.L0.u,
+                                                        R.L0.v, R.L0.w);
+    UF_CUDA(cudaGetLastError());
+    return UF_OK;
+  }
+
   uf_status adjoint_run(void* wsp, size_t bytes, int nsteps, int C, double z_lo, double z_hi, double u_hi, double u_lo,
                         void* dJ_dphi, double* J_out) override {
     if (!(d.fixed_dt > 0)) return fail(UF_ERR_ARG, "uf_adjoint_run needs a fixed time step (fixed_dt > 0)");
@@ -816,36 +921,10 @@ class GridImpl final : public uf_grid {
     T* base = reinterpret_cast<T*>(round_up(reinterpret_cast<size_t>(wsp), 256));
     uf_status s = build_step_graphs();
     if (s != UF_OK) return s;
-    // adjoint arrays
-    T* lam = base + A.lam;
-    FaceSet L0 = faces_at(lam), L1 = faces_at(lam + A.faceN), Lt = faces_at(lam + 2 * A.faceN),
-            L2 = faces_at(lam + 3 * A.faceN), Lh = faces_at(lam + 4 * A.faceN);
-    T* cells = lam + 5 * A.faceN;
-    T *lk0 = cells, *lk1 = cells + A.cellN, *lo0 = cells + 2 * A.cellN, *lo1 = cells + 3 * A.cellN;
-    T *lnut = cells + 4 * A.cellN, *lc = cells + 5 * A.cellN, *mu = cells + 6 * A.cellN, *badj = cells + 7 * A.cellN;
-    T* lphi = cells + 8 * A.cellN;
-    // the adjoint pressure solve: its own graph over (badj -> mu)
-    if (!adj_solve_exec || adj_mu != mu || adj_b != badj) {
-      if (adj_solve_exec) cudaGraphExecDestroy(adj_solve_exec);
-      adj_solve_exec = nullptr;
-      sol_x = mu;
-      sol_b = badj;
-      int nf, ns, ni;
-      auto pre = [&](cudaStream_t s2) {
-        int zc;
-        dim3 g = chunk_grid(d.nx, d.ny, d.nz, &zc);
-        uf::k_solve_reset<T><<<g, dim3(uf::BX, uf::BY), 0, s2>>>(lv[0], badj, zc, partials, st);
-        rec_count++;
-      };
-      s = capture(&adj_solve_exec, pre, [&](cudaStream_t) {}, &nf, &ns, &ni);
-      sol_x = p;
-      sol_b = b;
-      if (s != UF_OK) return s;
-      adj_mu = mu;
-      adj_b = badj;
-    }
-    const size_t faceB = A.faceN * sizeof(T), cellB = A.cellN * sizeof(T);
-    UF_CUDA(cudaMemsetAsync(lam, 0, (5 * A.faceN + 9 * A.cellN) * sizeof(T), stream));
+    AdjArrays R = adj_arrays(base, A);
+    s = ensure_adj_solve(R.mu, R.badj);
+    if (s != UF_OK) return s;
+    UF_CUDA(cudaMemsetAsync(base + A.lam, 0, (5 * A.faceN + 9 * A.cellN) * sizeof(T), stream));
     // 1. forward sweep with checkpoints every C steps
     for (int n = 0; n < nsteps; ++n) {
       if (n % C == 0) UF_CUDA(save_state(base + A.ckpt0 + (size_t)(n / C) * A.ckpt, A));
@@ -868,78 +947,77 @@ class GridImpl final : public uf_grid {
     const dim3 blk(uf::BX, uf::BY);
     if (k_hi >= k_lo)
       uf::k_objective_adj<T><<<plane_grid(d.nx, d.ny, k_hi - k_lo + 1), blk, 0, stream>>>(sp, u, v, w, k_lo, k_hi, u_hi,
-                                                                                          u_lo, L1.u, L1.v, L1.w);
+                                                                                          u_lo, R.L1.u, R.L1.v, R.L1.w);
     UF_CUDA(cudaGetLastError());
     // 3. reverse sweep, one checkpoint segment at a time
-    const dim3 gc = plane_grid(d.nx, d.ny, d.nz);
-    const dim3 ga = plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1);
     for (int seg = A.nseg - 1; seg >= 0; --seg) {
       const int n0 = seg * C, n1 = std::min(nsteps, n0 + C);
       UF_CUDA(load_state(base + A.ckpt0 + (size_t)seg * A.ckpt, A));
       for (int n = n0; n < n1; ++n) {   // recompute the segment, taping each step
-        T* t = base + A.tape0 + (size_t)(n - n0) * A.slot;
-        UF_CUDA(save_state(t, A));
-        UF_CUDA(cudaGraphLaunch(step_exec[parity], stream));
-        parity ^= 1;
-        UF_CUDA(copy_cell(t + A.s_nut, nut));
-        UF_CUDA(copy_faces(faces_at(t + A.s_uh), uh, vh, wh));
-        UF_CUDA(copy_faces(faces_at(t + A.s_ut), ut, vt, wt));
-        UF_CUDA(copy_faces(faces_at(t + A.s_u2), u2, v2, w2));
-        UF_CUDA(copy_faces(faces_at(t + A.s_u1), u, v, w));
+        s = tape_step(base + A.tape0 + (size_t)(n - n0) * A.slot, A);
+        if (s != UF_OK) return s;
       }
       for (int n = n1 - 1; n >= n0; --n) {
-        T* t = base + A.tape0 + (size_t)(n - n0) * A.slot;
-        const FaceSet U0 = faces_at(t);
-        const T* K0 = t + A.faceN;
-        const T* O0 = t + A.faceN + A.cellN;
-        const T* NUT = t + A.s_nut;
-        const FaceSet UH = faces_at(t + A.s_uh);
-        const FaceSet UT = faces_at(t + A.s_ut);
-        const FaceSet U2 = faces_at(t + A.s_u2);
-        const FaceSet U1 = faces_at(t + A.s_u1);
-        UF_CUDA(cudaMemsetAsync(L0.u, 0, faceB, stream));
-        UF_CUDA(cudaMemsetAsync(Lt.u, 0, 3 * faceB, stream));   // Lt, L2, Lh are contiguous
-        UF_CUDA(cudaMemsetAsync(lk0, 0, cellB, stream));
-        UF_CUDA(cudaMemsetAsync(lo0, 0, cellB, stream));
-        UF_CUDA(cudaMemsetAsync(lnut, 0, cellB, stream));
-        // a9^T: k-omega update
-        uf::k_turbulence_adj<T><<<gc, blk, 0, stream>>>(sp, U1.u, U1.v, U1.w, K0, O0, lk1, lo1, lk0, lo0, L1.u, L1.v,
-                                                        L1.w);
-        // a8^T: projection (A symmetric: the same MG-PCG)
-        uf::k_proj_adj_rhs<T><<<gc, blk, 0, stream>>>(sp, L1.u, L1.v, L1.w, badj);
-        UF_CUDA(cudaGraphLaunch(adj_solve_exec, stream));
-        uf::k_proj_adj_apply<T><<<ga, blk, 0, stream>>>(sp, mu, L1.u, L1.v, L1.w);
-        // a4/a5^T: drag and velocity BCs
-        uf::k_drag_bc_adj<T><<<ga, blk, 0, stream>>>(sp, U2.u, U2.v, U2.w, cc, L1.u, L1.v, L1.w, L2.u, L2.v, L2.w, lc);
-        // a3^T: diffusion
-        uf::k_diffuse_adj<T><<<ga, blk, 0, stream>>>(sp, UT.u, UT.v, UT.w, NUT, L2.u, L2.v, L2.w, Lt.u, Lt.v, Lt.w,
-                                                     lnut);
-        // a2^T: MacCormack advection
-        uf::AdvectArgs<T> Aa = advect_args();
-        Aa.u = U0.u; Aa.v = U0.v; Aa.w = U0.w;
-        Aa.uh = UH.u; Aa.vh = UH.v; Aa.wh = UH.w;
-        uf::AdvectAdj<T> Ja{Lt.u, Lt.v, Lt.w, Lh.u, Lh.v, Lh.w, L0.u, L0.v, L0.w};
-        uf::k_advect_backward_adj<T><<<ga, blk, 0, stream>>>(Aa, Ja);
-        uf::k_advect_forward_adj<T><<<ga, blk, 0, stream>>>(Aa, Ja);
-        // a1^T: eddy viscosity
-        uf::k_eddy_viscosity_adj<T><<<gc, blk, 0, stream>>>(sp, U0.u, U0.v, U0.w, K0, O0, lnut, lk0, lo0, L0.u, L0.v,
-                                                            L0.w);
-        UF_CUDA(cudaGetLastError());
-        std::swap(L0, L1);
-        std::swap(lk0, lk1);
-        std::swap(lo0, lo1);
+        s = reverse_step(base + A.tape0 + (size_t)(n - n0) * A.slot, A, R);
+        if (s != UF_OK) return s;
+        std::swap(R.L0, R.L1);
+        std::swap(R.lk0, R.lk1);
+        std::swap(R.lo0, R.lo1);
       }
       s = check_device(nullptr);
       if (s != UF_OK) return s;
     }
     // 4. dJ/dphi = dJ/dc dc/dphi; leave the grid at the final state
-    uf::k_dphi<T><<<(unsigned)((P.n_c + 255) / 256), 256, 0, stream>>>(phi, lc, lphi, P.n_c, d.Cd, d.a, d.b, d.e);
+    uf::k_dphi<T><<<(unsigned)((P.n_c + 255) / 256), 256, 0, stream>>>(phi, R.lc, R.lphi, P.n_c, d.Cd, d.a, d.b, d.e);
     UF_CUDA(cudaGetLastError());
     UF_CUDA(load_state(base + A.fin, A));
     if (dJ_dphi) {
-      s = copy_out(dJ_dphi, lphi, d.nx, d.ny, d.nz, P.Pc);
+      s = copy_out(dJ_dphi, R.lphi, d.nx, d.ny, d.nz, P.Pc);
       if (s != UF_OK) return s;
     }
+    return check_device(nullptr);
+  }
+
+  // Vector-Jacobian product of one step at the current state; the state is
+  // restored afterwards.  Order of the five arrays: u, v, w, k, omega.
+  uf_status step_vjp(void* wsp, size_t bytes, const void* const* lam_out, void* const* lam_in, void* lam_phi) override {
+    if (!(d.fixed_dt > 0)) return fail(UF_ERR_ARG, "uf_step_vjp needs a fixed time step (fixed_dt > 0)");
+    if (!have_state) return fail(UF_ERR_STATE, "no state: call uf_init_state or uf_set_state first");
+    if (!wsp || !lam_out || !lam_in) return fail(UF_ERR_ARG, "NULL workspace or cotangent arrays");
+    for (int q = 0; q < 5; ++q)
+      if (!lam_out[q] || !lam_in[q]) return fail(UF_ERR_ARG, "NULL cotangent array");
+    if (bytes < adjoint_bytes(1, 1)) return fail(UF_ERR_NOMEM, "workspace smaller than uf_adjoint_workspace_bytes(g, 1, 1)");
+    const AdjLayout A = adj_layout(1, 1);
+    T* base = reinterpret_cast<T*>(round_up(reinterpret_cast<size_t>(wsp), 256));
+    uf_status s = build_step_graphs();
+    if (s != UF_OK) return s;
+    AdjArrays R = adj_arrays(base, A);
+    s = ensure_adj_solve(R.mu, R.badj);
+    if (s != UF_OK) return s;
+    UF_CUDA(cudaMemsetAsync(base + A.lam, 0, (5 * A.faceN + 9 * A.cellN) * sizeof(T), stream));
+    T* keep = base + A.ckpt0;
+    UF_CUDA(save_state(keep, A));
+    T* t = base + A.tape0;
+    s = tape_step(t, A);
+    if (s == UF_OK) s = copy_in(R.L1.u, d.nx + 1, d.ny, d.nz, P.Pu, lam_out[0]);
+    if (s == UF_OK) s = copy_in(R.L1.v, d.nx, d.ny + 1, d.nz, P.Pc, lam_out[1]);
+    if (s == UF_OK) s = copy_in(R.L1.w, d.nx, d.ny, d.nz + 1, P.Pc, lam_out[2]);
+    if (s == UF_OK) s = copy_in(R.lk1, d.nx, d.ny, d.nz, P.Pc, lam_out[3]);
+    if (s == UF_OK) s = copy_in(R.lo1, d.nx, d.ny, d.nz, P.Pc, lam_out[4]);
+    if (s == UF_OK) s = reverse_step(t, A, R);
+    if (s == UF_OK) s = copy_out(lam_in[0], R.L0.u, d.nx + 1, d.ny, d.nz, P.Pu);
+    if (s == UF_OK) s = copy_out(lam_in[1], R.L0.v, d.nx, d.ny + 1, d.nz, P.Pc);
+    if (s == UF_OK) s = copy_out(lam_in[2], R.L0.w, d.nx, d.ny, d.nz + 1, P.Pc);
+    if (s == UF_OK) s = copy_out(lam_in[3], R.lk0, d.nx, d.ny, d.nz, P.Pc);
+    if (s == UF_OK) s = copy_out(lam_in[4], R.lo0, d.nx, d.ny, d.nz, P.Pc);
+    if (s == UF_OK && lam_phi) {
+      uf::k_dphi<T><<<(unsigned)((P.n_c + 255) / 256), 256, 0, stream>>>(phi, R.lc, R.lphi, P.n_c, d.Cd, d.a, d.b,
+                                                                         d.e);
+      UF_CUDA(cudaGetLastError());
+      s = copy_out(lam_phi, R.lphi, d.nx, d.ny, d.nz, P.Pc);
+    }
+    UF_CUDA(load_state(keep, A));   // the grid keeps its state
+    if (s != UF_OK) return s;
     return check_device(nullptr);
   }
 
@@ -1519,6 +1597,11 @@ uf_status uf_adjoint_run(uf_grid* g, void* ws, size_t bytes, int nsteps, int ckp
                          double u_hi, double u_lo, void* dJ_dphi, double* J_out) {
   UF_NEED(g);
   return g->adjoint_run(ws, bytes, nsteps, ckpt_every, z_lo, z_hi, u_hi, u_lo, dJ_dphi, J_out);
+}
+uf_status uf_step_vjp(uf_grid* g, void* d_ws, size_t bytes, const void* const* lam_out, void* const* lam_in,
+                      void* lam_phi) {
+  UF_NEED(g);
+  return g->step_vjp(d_ws, bytes, lam_out, lam_in, lam_phi);
 }
 uf_status uf_get_tuning(uf_grid* g, uf_tuning* out, int* levels) {
   UF_NEED(g);

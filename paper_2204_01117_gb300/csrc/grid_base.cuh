@@ -53,6 +53,7 @@ struct uf_grid {
   virtual uf_status profile_step(uf_kernel_time*, int, int*, uf_step_stats*) = 0;
   virtual size_t adjoint_bytes(int, int) = 0;
   virtual uf_status adjoint_run(void*, size_t, int, int, double, double, double, double, void*, double*) = 0;
+  virtual uf_status step_vjp(void*, size_t, const void* const*, void* const*, void*) = 0;
   virtual uf_status design_phi(int, const double*, const double*, double, void*) = 0;
   virtual uf_status design_vjp(int, const double*, const double*, double, const void*, double*) = 0;
   virtual uf_status get_tuning(uf_tuning*, int*) = 0;

@@ -158,6 +158,8 @@ def load():
     lib.uf_adjoint_workspace_bytes.restype = ctypes.c_size_t
     lib.uf_adjoint_run.argtypes = [vp, vp, ctypes.c_size_t, ip, ip, dp, dp, dp, dp, vp, P(dp)]
     lib.uf_adjoint_run.restype = ip
+    lib.uf_step_vjp.argtypes = [vp, vp, ctypes.c_size_t, P(vp), P(vp), vp]
+    lib.uf_step_vjp.restype = ip
     lib.uf_design_to_phi.argtypes = [vp, ip, P(dp), P(dp), dp, vp]
     lib.uf_design_to_phi.restype = ip
     lib.uf_design_vjp.argtypes = [vp, ip, P(dp), P(dp), dp, vp, P(dp)]
@@ -437,6 +439,32 @@ class Grid:
         check(self.lib.uf_adjoint_run(self._h, ctypes.c_void_p(ws.data_ptr()), nbytes, nsteps, ckpt_every, z_lo, z_hi,
                                       u_hi, u_lo, optr, ctypes.byref(J)))
         return J.value, out
+
+    STATE5 = ("u", "v", "w", "k", "omega")
+
+    def step_vjp(self, lam_out: dict, with_phi: bool = False):
+        """Cotangents of one step's input state (and of phi) from the
+        cotangent of its output state; dicts keyed u, v, w, k, omega."""
+        import torch
+        nbytes = int(self.lib.uf_adjoint_workspace_bytes(self._h, 1, 1))
+        ws = getattr(self, "_adj_ws", None)
+        if ws is None or ws.numel() < nbytes:
+            self._adj_ws = None
+            ws = self._adj_ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        keep = []
+        outs = (ctypes.c_void_p * 5)()
+        ins = (ctypes.c_void_p * 5)()
+        lam_in = {}
+        for q, n in enumerate(self.STATE5):
+            ptr, k = self._arg(np.asarray(lam_out[n], dtype=self.np_dtype).reshape(self.shapes[n]))
+            keep.append(k)
+            outs[q] = ptr
+            lam_in[n] = np.empty(self.shapes[n], dtype=self.np_dtype)
+            ins[q] = lam_in[n].ctypes.data
+        lphi = np.empty(self.shapes["phi"], dtype=self.np_dtype) if with_phi else None
+        check(self.lib.uf_step_vjp(self._h, ctypes.c_void_p(ws.data_ptr()), nbytes, outs, ins,
+                                   ctypes.c_void_p(lphi.ctypes.data) if with_phi else None))
+        return (lam_in, lphi) if with_phi else lam_in
 
     def free_adjoint_workspace(self) -> None:
         self._adj_ws = None

@@ -221,3 +221,119 @@ def test_adjoint_needs_fixed_dt():
     with pytest.raises(uf.UFError) as ei:
         g.adjoint_run(2)
     assert ei.value.status == uf.UF_ERR_ARG
+
+
+STATE5 = ("u", "v", "w", "k", "omega")
+
+
+def _small_grid():
+    """8 x 8 x 8, two inflow sides (wind 30 deg), a porous block, FP64 with
+    the CG tolerance at 1e-14 so that central differences resolve 1e-9."""
+    n = 8
+    g = uf.Grid(n, n, n, precision="f64", h=2.0, wind_dir_deg=30.0, u_ref=3.0, z_ref=10.0, z0=0.5, inflow_loglaw=1,
+                ground_noslip=1, fixed_dt=0.2, cg_tol=1e-14)
+    phi = np.ones((n, n, n))
+    phi[0:4, 3:6, 3:6] = 0.5
+    g.set_porosity(phi)
+    g.init_state()
+    g.run(2)
+    return g
+
+
+def _flat(st):
+    return np.concatenate([np.asarray(st[n], dtype=np.float64).ravel() for n in STATE5])
+
+
+def _unflat(x, g):
+    out, o = {}, 0
+    for n in STATE5:
+        m = int(np.prod(g.shapes[n]))
+        out[n] = x[o:o + m].reshape(g.shapes[n])
+        o += m
+    return out
+
+
+def test_step_vjp_dense_jacobian_transpose_8cubed():
+    """Every row of (dX'/dX)^T from uf_step_vjp against every column of the
+    central-difference Jacobian of one FP64 step at 8^3 (2752 state values).
+
+    The step is piecewise smooth: a semi-Lagrangian sample is trilinear, so
+    linear between lattice planes with a kink where the departure point
+    crosses one (a velocity of zero puts it on a plane).  The check runs at
+    a generic state: the developed flow plus seeded noise, with every
+    velocity at least 1e-4 m/s away from zero, far beyond the 1e-6 steps."""
+    g = _small_grid()
+    x0 = g.state()
+    p0 = x0["p"]
+    rng = np.random.default_rng(8)
+    for n in ("u", "v", "w"):
+        a = x0[n] + 0.02 * rng.standard_normal(x0[n].shape)
+        x0[n] = np.where(np.abs(a) < 1e-4, 1e-4, a)
+    for n in ("k", "omega"):
+        x0[n] = x0[n] * (1.0 + 0.01 * rng.standard_normal(x0[n].shape))
+    x = _flat(x0)
+    N = x.size
+
+    def step_of(xv):
+        g.set_fields(dict(_unflat(xv, g), p=p0))
+        g.step(stats=False)
+        return _flat(g.state())
+
+    J_fd = np.empty((N, N))
+    for j in range(N):
+        e = 1e-6 * max(1.0, abs(x[j]))
+        xp, xm = x.copy(), x.copy()
+        xp[j] += e
+        xm[j] -= e
+        J_fd[:, j] = (step_of(xp) - step_of(xm)) / (2 * e)
+    g.set_fields(x0)
+    J_ad = np.empty((N, N))
+    for i in range(N):
+        lam = np.zeros(N)
+        lam[i] = 1.0
+        J_ad[i, :] = _flat(g.step_vjp(_unflat(lam, g)))
+    scale = np.abs(J_fd).max()
+    err = np.abs(J_ad - J_fd)
+    assert np.linalg.norm(J_ad - J_fd) <= 1e-7 * np.linalg.norm(J_fd), np.unravel_index(err.argmax(), err.shape)
+    assert err.max() <= 1e-6 * scale, (np.unravel_index(err.argmax(), err.shape), err.max(), scale)
+
+
+def test_step_vjp_dot_product_and_state_untouched():
+    """<w, J v> by central differences against <J^T w, v> on the 24 x 20 x 10
+    design grid; the grid's state is bitwise unchanged by uf_step_vjp."""
+    g = grid()
+    x0 = start_state(g)
+    g.set_fields(x0)
+    before = g.state()
+    rng = np.random.default_rng(3)
+    x = _flat(x0)
+    v = rng.standard_normal(x.size) * (np.abs(x) + 1e-3)
+    w = rng.standard_normal(x.size)
+    lam_in, lam_phi = g.step_vjp(_unflat(w, g), with_phi=True)
+    after = g.state()
+    for f in ("u", "v", "w", "p", "k", "omega"):
+        np.testing.assert_array_equal(after[f], before[f], err_msg=f)
+    eps = 1e-7
+
+    def step_of(xv):
+        g.set_fields(dict(_unflat(xv, g), p=x0["p"]))
+        g.step(stats=False)
+        return _flat(g.state())
+
+    jv = (step_of(x + eps * v) - step_of(x - eps * v)) / (2 * eps)
+    lhs = float(np.dot(w, jv))
+    rhs = float(np.dot(_flat(lam_in), v))
+    assert rhs == pytest.approx(lhs, rel=1e-6), (lhs, rhs)
+    # and the porosity part, against a porosity perturbation
+    phi = g.get_state("phi")
+    dphi = rng.standard_normal(phi.shape) * phi * (1 - phi)
+
+    def step_phi(ph):
+        g.set_porosity(ph)
+        g.set_fields(x0)
+        g.step(stats=False)
+        return _flat(g.state())
+
+    jp = (step_phi(phi + 1e-6 * dphi) - step_phi(phi - 1e-6 * dphi)) / 2e-6
+    g.set_porosity(phi)
+    assert float(np.sum(lam_phi * dphi)) == pytest.approx(float(np.dot(w, jp)), rel=1e-6)
