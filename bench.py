@@ -445,7 +445,7 @@ def run_ours(args):
         "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config({"parallelism": f"replicas x{world}", "cg_iters_last_step": st1.cg_iters,
-                                   "precond": "MG V-cycle (damped Jacobi 2+2)", "cg_tol": 1e-7}),
+                                   "precond": "MG V-cycle (2+2 Chebyshev-weighted Jacobi)", "cg_tol": 1e-7}),
         "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"hbm_gbs of {peak_kind}",

@@ -95,11 +95,13 @@ typedef struct {
   double ai_omega;         /* relaxation of the AI preconditioner           */
   double mg_jacobi_omega;  /* damping of the MG Jacobi smoother (6/7)       */
   int mg_coarse_max;       /* coarsest MG level has at most this many cells */
-  int mg_smoother;         /* UF_SMOOTH_JACOBI (default) or UF_SMOOTH_RBGS  */
+  int mg_smoother;         /* UF_SMOOTH_CHEBY (default), _JACOBI or _RBGS   */
 } uf_grid_desc;
 
 enum { UF_SMOOTH_JACOBI = 0,   /* damped Jacobi, 2 sweeps before + 2 after        */
-       UF_SMOOTH_RBGS = 1 };   /* red-black Gauss-Seidel, red-black / black-red   */
+       UF_SMOOTH_RBGS = 1,     /* red-black Gauss-Seidel, red-black / black-red   */
+       UF_SMOOTH_CHEBY = 2 };  /* 2 weighted-Jacobi sweeps before + 2 after with
+                                  the degree-2 Chebyshev weights for [1/3, 2]   */
 
 typedef struct {
   double dt;               /* time step taken                                */

@@ -178,7 +178,7 @@ struct CgP {     // CG initial residual, direction + A d
 template <typename T>
 struct MgP {     // V-cycle level kernels
   uf::Level<T> F, C;
-  T omega;
+  uf::SmoothW<T> sw;
   T* x;
   const T *d0, *d1, *q;
   T* out;
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(uf::FT, 4) kb_mg_down(const __grid_constant__ 
                                                      cudaGraphConditionalHandle cond, int use_cond, int* left) {
   for_items(&A.m, [&](int i, int zc, const VBlock& vb) {
     const MgP<T>& P = A.at[i];
-    uf::mg_down_body<T, SM, CG>(P.F, P.C, P.omega, zc, P.x, P.d0, P.d1, P.q, P.partials, P.st, cond, use_cond,
+    uf::mg_down_body<T, SM, CG>(P.F, P.C, P.sw, zc, P.x, P.d0, P.d1, P.q, P.partials, P.st, cond, use_cond,
                                 CG ? left : nullptr, vb);
   });
 }
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(uf::TAIL_T) kb_mg_tail(const View<T>* __restri
                                                          const LaunchMap* __restrict__ m) {
   for_items(m, [&](int i, int, const VBlock& vb) {
     const View<T>& G = V[i];
-    uf::mg_tail_body<T, SM>(G.tail, G.omega, G.st, vb);
+    uf::mg_tail_body<T, SM>(G.tail, G.sw, G.st, vb);
   });
 }
 
@@ -288,7 +288,7 @@ template <typename T, int SM, bool FINEST>
 __global__ void __launch_bounds__(uf::FT, 4) kb_mg_up(const __grid_constant__ Args<MgP<T>> A, int mode) {
   for_items(&A.m, [&](int i, int zc, const VBlock& vb) {
     const MgP<T>& P = A.at[i];
-    uf::mg_up_body<T, SM, FINEST>(P.F, P.C, P.omega, zc, P.out, mode, P.partials, P.st, vb);
+    uf::mg_up_body<T, SM, FINEST>(P.F, P.C, P.sw, zc, P.out, mode, P.partials, P.st, vb);
   });
 }
 
@@ -522,7 +522,7 @@ class BatchImpl final : public uf_batch {
     std::memset(&P, 0, sizeof(P));
     P.F = G.lv[l];
     P.C = G.lv[l + 1];
-    P.omega = G.omega;
+    P.sw = G.sw;
     P.partials = G.partials;
     P.st = G.st;
     return P;
@@ -581,8 +581,8 @@ class BatchImpl final : public uf_batch {
   }
 
   void vcycle(cudaStream_t s, int mode, cudaGraphConditionalHandle cond, int use_cond) {
-    if (smoother == UF_SMOOTH_JACOBI) rec_vcycle<uf::SM_JACOBI>(s, mode, cond, use_cond);
-    else rec_vcycle<uf::SM_RBGS>(s, mode, cond, use_cond);
+    if (smoother == UF_SMOOTH_RBGS) rec_vcycle<uf::SM_RBGS>(s, mode, cond, use_cond);
+    else rec_vcycle<uf::SM_JACOBI>(s, mode, cond, use_cond);
   }
 
   double plane_bytes(int kind, double per_cell) const {

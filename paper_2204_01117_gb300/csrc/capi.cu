@@ -89,7 +89,10 @@ bool desc_valid(const uf_grid_desc* d, std::string* why) {
   if (d->inflow_loglaw && !(d->z0 > 0 && d->z_ref > d->z0)) { *why = "log law needs z_ref > z0 > 0"; return false; }
   if (d->precond < UF_PRECOND_MG || d->precond > UF_PRECOND_NONE) { *why = "unknown preconditioner"; return false; }
   if (!(d->cg_tol >= 0) || d->cg_max_iter < 1) { *why = "cg_tol >= 0 and cg_max_iter >= 1 required"; return false; }
-  if (d->mg_smoother != UF_SMOOTH_JACOBI && d->mg_smoother != UF_SMOOTH_RBGS) { *why = "unknown smoother"; return false; }
+  if (d->mg_smoother != UF_SMOOTH_JACOBI && d->mg_smoother != UF_SMOOTH_RBGS && d->mg_smoother != UF_SMOOTH_CHEBY) {
+    *why = "unknown smoother";
+    return false;
+  }
   if (!(d->ai_omega > 0 && d->ai_omega < 2)) { *why = "ai_omega must lie in (0, 2)"; return false; }
   if (!(d->mg_jacobi_omega > 0 && d->mg_jacobi_omega <= 1)) { *why = "mg_jacobi_omega must lie in (0, 1]"; return false; }
   if (d->mg_coarse_max < 1 || d->mg_coarse_max > 1024) { *why = "mg_coarse_max must lie in [1, 1024]"; return false; }
@@ -510,9 +513,31 @@ class GridImpl final : public uf_grid {
   // Fused V-cycle: down kernels to the tail level, the tail, up kernels.
   // mode 1 (inside the CG loop): the finest down kernel also applies the CG
   // update and the convergence test.
+  // Weights of the two smoothing sweeps.  Damped Jacobi: both mg_jacobi_omega.
+  // Chebyshev: on the 7-point operator, the modes with a high frequency
+  // (theta >= pi/2) along at least one axis have eigenvalues of D^-1 A in
+  // [1/3, 2]; the weights are the reciprocals of the roots of the degree-2
+  // Chebyshev polynomial on that interval, c +- h cos(pi/4), which damp those
+  // modes by 1/T2(7/5) = 0.342 per pair of sweeps against (5/7)^2 = 0.510
+  // for two sweeps at the best single weight 6/7.
+  uf::SmoothW<T> smooth_weights() const {
+    double w1 = d.mg_jacobi_omega, w2 = d.mg_jacobi_omega;
+    if (d.mg_smoother == UF_SMOOTH_CHEBY) {
+      const double lo = 1.0 / 3.0, hi = 2.0, c = 0.5 * (lo + hi), h = 0.5 * (hi - lo), r = std::sqrt(0.5);
+      w1 = 1.0 / (c + h * r);
+      w2 = 1.0 / (c - h * r);
+    }
+    uf::SmoothW<T> W;
+    W.pa = (T)(w1 + w2 - w1 * w2);
+    W.pb = (T)(w1 * w2);
+    W.w1 = (T)w1;
+    W.w2 = (T)w2;
+    return W;
+  }
+
   template <int SM>
   void rec_vcycle_sm(cudaStream_t s, int mode, cudaGraphConditionalHandle cond, int use_cond) {
-    const T om = (T)d.mg_jacobi_omega;
+    const uf::SmoothW<T> om = smooth_weights();
     const int lt = P.tail_level;
     for (int l = 0; l < lt; ++l) {
       const std::string sl = std::to_string(l);
@@ -546,8 +571,8 @@ class GridImpl final : public uf_grid {
     }
   }
   void rec_vcycle(cudaStream_t s, int mode, cudaGraphConditionalHandle cond, int use_cond) {
-    if (d.mg_smoother == UF_SMOOTH_JACOBI) rec_vcycle_sm<uf::SM_JACOBI>(s, mode, cond, use_cond);
-    else rec_vcycle_sm<uf::SM_RBGS>(s, mode, cond, use_cond);
+    if (d.mg_smoother == UF_SMOOTH_RBGS) rec_vcycle_sm<uf::SM_RBGS>(s, mode, cond, use_cond);
+    else rec_vcycle_sm<uf::SM_JACOBI>(s, mode, cond, use_cond);
   }
 
   // Non-multigrid preconditioners (one kernel, which also forms r.z).
@@ -1281,7 +1306,7 @@ class GridImpl final : public uf_grid {
     V.partials = partials;
     V.dt = dt;
     V.dtT = dtT;
-    V.omega = (T)d.mg_jacobi_omega;
+    V.sw = smooth_weights();
   }
 
   // ------------------------------------------------------------ entry points
@@ -1519,7 +1544,7 @@ void uf_default_desc(uf_grid_desc* d) {
   d->cfl = 0.5; d->fixed_dt = 0.0; d->k_min = 1e-10; d->omega_min = 1e-6;
   d->precond = UF_PRECOND_MG; d->cg_tol = 0.0; d->cg_max_iter = 200;
   d->ai_omega = 1.65; d->mg_jacobi_omega = 6.0 / 7.0; d->mg_coarse_max = 512;
-  d->mg_smoother = UF_SMOOTH_JACOBI;
+  d->mg_smoother = UF_SMOOTH_CHEBY;
 }
 
 size_t uf_workspace_bytes(const uf_grid_desc* d) {

@@ -33,7 +33,7 @@ struct GridView {
   double* partials;
   double* dt;
   T* dtT;
-  T omega;                         // damped-Jacobi weight of the smoother
+  uf::SmoothW<T> sw;               // smoother weights
 };
 
 struct uf_grid {

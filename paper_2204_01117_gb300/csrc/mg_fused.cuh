@@ -112,15 +112,28 @@ __device__ __forceinline__ T diag_z(const Level<T>& L, int k) {
   return D;
 }
 
-// Pre-smoothing from zero with q = r/D staged: Jacobi x2 = w(2-w) q_c +
-// w^2/D_c sum w_a q_nb;  RBGS red q_c, black q_c + sum w_a q_nb / D_c.
+// Weights of the two weighted-Jacobi sweeps x <- x + w_k D^-1 (r - A x)
+// (k = 1, 2).  From x = 0 the pair gives x2 = pa q + pb D^-1 sum w_a q_nb
+// with q = r/D, pa = w1 + w2 - w1 w2 and pb = w1 w2.  Damped Jacobi: w1 = w2
+// = w.  Chebyshev: the roots of the degree-2 Chebyshev polynomial on the
+// high-frequency range of D^-1 A (see the host side).  The two factors
+// commute, so post-smoothing with the same weights keeps the V-cycle
+// symmetric.
+template <typename T>
+struct SmoothW {
+  T pa, pb;   // pre-smoothing from zero
+  T w1, w2;   // post-smoothing passes
+};
+
+// Pre-smoothing from zero with q = r/D staged: weighted Jacobi x2 = pa q_c +
+// pb/D_c sum w_a q_nb;  RBGS red q_c, black q_c + sum w_a q_nb / D_c.
 template <int SM, typename T>
-__device__ __forceinline__ T presmooth(T qc, T s, T D, T omega, bool red) {
-  if (SM == SM_JACOBI) return omega * (T(2) - omega) * qc + omega * omega * s / D;
+__device__ __forceinline__ T presmooth(T qc, T s, T D, const SmoothW<T>& W, bool red) {
+  if (SM == SM_JACOBI) return W.pa * qc + W.pb * s / D;
   return red ? qc : qc + s / D;
 }
-// Post-smoothing pass on t: Jacobi t + w (r - D t + s)/D; RBGS relaxes the
-// colour `relax` and keeps the other.
+// Post-smoothing pass on t: weighted Jacobi t + w (r - D t + s)/D; RBGS
+// relaxes the colour `relax` and keeps the other.
 template <int SM, typename T>
 __device__ __forceinline__ T relax(T tc, T rc, T s, T D, T omega, bool active) {
   if (SM == SM_JACOBI) return tc + omega * (rc - D * tc + s) / D;
@@ -143,7 +156,7 @@ __device__ __forceinline__ int ring3(int k) { return ((k % 3) + 3) % 3; }
 __device__ __forceinline__ int ring4(int k) { return (k + 4) & 3; }
 
 template <typename T, int SM, bool CG>
-__device__ __forceinline__ void mg_down_body(const Level<T>& F, const Level<T>& C, T omega, int zc, T* __restrict__ x,
+__device__ __forceinline__ void mg_down_body(const Level<T>& F, const Level<T>& C, const SmoothW<T>& W, int zc, T* __restrict__ x,
                                              const T* d0, const T* d1, const T* __restrict__ q, double* partials,
                                              SolveState* st, cudaGraphConditionalHandle cond, int use_cond,
                                              int* left, const VBlock& vb) {
@@ -230,7 +243,7 @@ __device__ __forceinline__ void mg_down_body(const Level<T>& F, const Level<T>& 
       if (kin && px[h].ok) {
         const int b = sxq[h];
         const T s = F.wx * (qc[b - 1] + qc[b + 1]) + F.wy * (qc[b - QX] + qc[b + QX]) + F.wz * (qm[b] + qp[b]);
-        v = presmooth<SM>(qc[b], s, px[h].dxy + dz, omega, ((par[h] + k) & 1) == 0);
+        v = presmooth<SM>(qc[b], s, px[h].dxy + dz, W, ((par[h] + k) & 1) == 0);
       }
       dst[sx[h]] = v;
     }
@@ -336,11 +349,11 @@ __device__ __forceinline__ void mg_down_body(const Level<T>& F, const Level<T>& 
 }
 
 template <typename T, int SM, bool CG>
-__global__ void __launch_bounds__(FT) k_mg_down(Level<T> F, Level<T> C, T omega, int zc, T* __restrict__ x,
+__global__ void __launch_bounds__(FT) k_mg_down(Level<T> F, Level<T> C, SmoothW<T> W, int zc, T* __restrict__ x,
                                                const T* d0, const T* d1, const T* __restrict__ q,
                                                double* partials, SolveState* st, cudaGraphConditionalHandle cond,
                                                int use_cond) {
-  mg_down_body<T, SM, CG>(F, C, omega, zc, x, d0, d1, q, partials, st, cond, use_cond, nullptr, vblock());
+  mg_down_body<T, SM, CG>(F, C, W, zc, x, d0, d1, q, partials, st, cond, use_cond, nullptr, vblock());
 }
 
 
@@ -350,7 +363,7 @@ __global__ void __launch_bounds__(FT) k_mg_down(Level<T> F, Level<T> C, T omega,
 // plane, written to `out` (F.t on coarse levels, z on the finest).
 // FINEST: also r.z and the CG beta.  Global loads run one plane ahead.
 template <typename T, int SM, bool FINEST>
-__device__ __forceinline__ void mg_up_body(const Level<T>& F, const Level<T>& C, T omega, int zc, T* __restrict__ out,
+__device__ __forceinline__ void mg_up_body(const Level<T>& F, const Level<T>& C, const SmoothW<T>& W, int zc, T* __restrict__ out,
                                            int mode, double* partials, SolveState* st, const VBlock& vb) {
   __shared__ T sT[4][QP];
   __shared__ T sU[3][XP];
@@ -426,7 +439,7 @@ __device__ __forceinline__ void mg_up_body(const Level<T>& F, const Level<T>& C,
       if (kin && pu[h].ok) {
         const int b = sut[h];
         const T s = F.wx * (tc[b - 1] + tc[b + 1]) + F.wy * (tc[b - QX] + tc[b + QX]) + F.wz * (tm[b] + tp[b]);
-        v = relax<SM>(tc[b], pr[h], s, pu[h].dxy + dz, omega, ((par[h] + k) & 1) == 1);
+        v = relax<SM>(tc[b], pr[h], s, pu[h].dxy + dz, W.w1, ((par[h] + k) & 1) == 1);
       }
       dst[su[h]] = v;
     }
@@ -463,7 +476,7 @@ __device__ __forceinline__ void mg_up_body(const Level<T>& F, const Level<T>& C,
       const T* uc = sU[ring3(k)];
       const T* up = sU[ring3(k + 1)];
       const T s = F.wx * (uc[b - 1] + uc[b + 1]) + F.wy * (uc[b - XX] + uc[b + XX]) + F.wz * (um[b] + up[b]);
-      const T zv = relax<SM>(uc[b], o_r, s, po.dxy + diag_z(F, k), omega, ((opar + k) & 1) == 0);
+      const T zv = relax<SM>(uc[b], o_r, s, po.dxy + diag_z(F, k), W.w2, ((opar + k) & 1) == 0);
       out[oc] = zv;
       if (FINEST) dacc.add(o_r, zv);
     }
@@ -484,9 +497,9 @@ __device__ __forceinline__ void mg_up_body(const Level<T>& F, const Level<T>& C,
 }
 
 template <typename T, int SM, bool FINEST>
-__global__ void __launch_bounds__(FT) k_mg_up(Level<T> F, Level<T> C, T omega, int zc, T* __restrict__ out, int mode,
+__global__ void __launch_bounds__(FT) k_mg_up(Level<T> F, Level<T> C, SmoothW<T> W, int zc, T* __restrict__ out, int mode,
                                              double* partials, SolveState* st) {
-  mg_up_body<T, SM, FINEST>(F, C, omega, zc, out, mode, partials, st, vblock());
+  mg_up_body<T, SM, FINEST>(F, C, W, zc, out, mode, partials, st, vblock());
 }
 
 
@@ -510,7 +523,8 @@ struct TailArgs {
 };
 
 template <typename T, int SM>
-__device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, T omega, const SolveState* st, const VBlock& vb) {
+__device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, const SmoothW<T>& W, const SolveState* st,
+                                             const VBlock& vb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* S = reinterpret_cast<T*>(smem_raw);
   if (st->converged) return;
@@ -561,7 +575,7 @@ __device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, T omega, cons
       const int i = e % L.nx, j = (e / L.nx) % L.ny, k = e / (L.nx * L.ny);
       const int b = (i + 1) + X * (j + 1) + P * (k + 1);
       const T s = L.wx * (u[b - 1] + u[b + 1]) + L.wy * (u[b - X] + u[b + X]) + L.wz * (u[b - P] + u[b + P]);
-      a[b] = presmooth<SM>(u[b], s, diag_of(L, i, j, k), omega, ((i + j + k) & 1) == 0);
+      a[b] = presmooth<SM>(u[b], s, diag_of(L, i, j, k), W, ((i + j + k) & 1) == 0);
     }
     __syncthreads();
     T* rc = S + A.off[m + 1];
@@ -627,14 +641,14 @@ __device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, T omega, cons
       const int i = e % L.nx, j = (e / L.nx) % L.ny, k = e / (L.nx * L.ny);
       const int b = (i + 1) + X * (j + 1) + P * (k + 1);
       const T s = L.wx * (a[b - 1] + a[b + 1]) + L.wy * (a[b - X] + a[b + X]) + L.wz * (a[b - P] + a[b + P]);
-      u[b] = relax<SM>(a[b], r[b], s, diag_of(L, i, j, k), omega, ((i + j + k) & 1) == 1);
+      u[b] = relax<SM>(a[b], r[b], s, diag_of(L, i, j, k), W.w1, ((i + j + k) & 1) == 1);
     }
     __syncthreads();
     for (int e = tid; e < n; e += TAIL_T) {
       const int i = e % L.nx, j = (e / L.nx) % L.ny, k = e / (L.nx * L.ny);
       const int b = (i + 1) + X * (j + 1) + P * (k + 1);
       const T s = L.wx * (u[b - 1] + u[b + 1]) + L.wy * (u[b - X] + u[b + X]) + L.wz * (u[b - P] + u[b + P]);
-      a[b] = relax<SM>(u[b], r[b], s, diag_of(L, i, j, k), omega, ((i + j + k) & 1) == 0);
+      a[b] = relax<SM>(u[b], r[b], s, diag_of(L, i, j, k), W.w2, ((i + j + k) & 1) == 0);
     }
     __syncthreads();
   }
@@ -652,8 +666,8 @@ __device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, T omega, cons
 }
 
 template <typename T, int SM>
-__global__ void __launch_bounds__(TAIL_T) k_mg_tail(TailArgs<T> A, T omega, const SolveState* st) {
-  mg_tail_body<T, SM>(A, omega, st, vblock());
+__global__ void __launch_bounds__(TAIL_T) k_mg_tail(TailArgs<T> A, SmoothW<T> W, const SolveState* st) {
+  mg_tail_body<T, SM>(A, W, st, vblock());
 }
 
 

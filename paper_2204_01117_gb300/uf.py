@@ -29,7 +29,7 @@ STATUS_NAMES = ["UF_OK", "UF_ERR_ARG", "UF_ERR_CUDA", "UF_ERR_NOMEM", "UF_ERR_NO
                 "UF_ERR_TIMEOUT", "UF_ERR_STATE"]
 F32, F64 = 0, 1
 PRECOND = {"mg": 0, "ai1": 1, "jacobi": 2, "none": 3}
-SMOOTHER = {"jacobi": 0, "rbgs": 1}
+SMOOTHER = {"jacobi": 0, "rbgs": 1, "cheby": 2}
 FIELDS = {"u": 0, "v": 1, "w": 2, "p": 3, "k": 4, "omega": 5, "phi": 6, "nut": 7}
 
 

@@ -28,7 +28,7 @@ def test_default_desc_paper_constants(lib):
     assert d.C_lim == 7.0 / 8.0
     assert (d.a, d.b, d.e, d.Cd) == (0.62, 2.5, 1e-10, 1.0)
     assert d.precond == uf.PRECOND["mg"] and d.cg_tol == 0.0 and d.cg_max_iter == 200
-    assert d.mg_smoother == uf.SMOOTHER["jacobi"]
+    assert d.mg_smoother == uf.SMOOTHER["cheby"]
     assert d.ai_omega == 1.65 and d.cfl == 0.5
 
 

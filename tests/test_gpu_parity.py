@@ -63,13 +63,13 @@ def test_poisson_operator(precision, dims, deg):
     assert rel(y, ref) <= tol
 
 
-@pytest.mark.parametrize("precond", ["mg", "mg-rbgs", "ai1", "jacobi", "none"])
+@pytest.mark.parametrize("precond", ["mg", "mg-rbgs", "mg-cheby", "ai1", "jacobi", "none"])
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_poisson_solve(precond, precision):
     nx, ny, nz = 45, 37, 11
     tol = 1e-12 if precision == "f64" else 1e-7
     o = oracle.Oracle(nx, ny, nz, wind_dir_deg=30.0)
-    extra = {"mg_smoother": "rbgs"} if precond == "mg-rbgs" else {}
+    extra = {"mg_smoother": precond.split("-")[1]} if precond.startswith("mg-") else {}
     g = uf.Grid(nx, ny, nz, precision=precision, wind_dir_deg=30.0, precond=precond.split("-")[0], cg_tol=tol,
                 cg_max_iter=5000, **extra)
     b = np.random.default_rng(1).standard_normal((nz, ny, nx))
