@@ -417,11 +417,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for n in names:
-            g.set_state(n, host_in[n])
+        g.put_fields(host_in)      # one contiguous copy per field, repacked on the device
         g.step(stats=False)
-        for n in names:
-            g.get_state(n, out=host_out[n])
+        g.take_fields(host_out)    # one synchronisation per step
     torch.cuda.synchronize()
     e2e_value, e2e_s = weak_scaling_rate(sc.cells, e2e_steps, time.perf_counter() - t0)
 

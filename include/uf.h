@@ -149,6 +149,18 @@ uf_status uf_set_porosity(uf_grid* g, const void* phi);
 uf_status uf_set_state(uf_grid* g, int field, const void* buf);
 uf_status uf_get_state(uf_grid* g, int field, void* buf);
 
+/* Several fields in (uf_set_fields) or out (uf_get_fields) in one call:
+ * fields[i] (UF_FIELD_*) from / to bufs[i], dense layout as uf_set_state
+ * (setting PHI also derives the drag coefficient).  A host buffer moves with
+ * one contiguous copy through a device staging array and is repacked to the
+ * padded layout by a kernel; a device buffer is repacked directly.  The
+ * staging arrays are scratch buffers of the step: call between steps, not
+ * concurrently with one.  uf_set_fields returns once the copies are
+ * enqueued (a pinned host buffer must stay valid until the stream has
+ * consumed it); uf_get_fields synchronises once, after the last field. */
+uf_status uf_set_fields(uf_grid* g, int n, const int* fields, const void* const* bufs);
+uf_status uf_get_fields(uf_grid* g, int n, const int* fields, void* const* bufs);
+
 /* Initial state: the inflow profile on every face (Dirichlet values on the
  * boundary faces), k and omega at the inlet values of Sec. 3
  * (k = 1.5 (I U)^2, omega = k^1/2 / (C_mu^1/4 L)), one drag step with the

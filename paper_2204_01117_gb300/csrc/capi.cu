@@ -1364,6 +1364,98 @@ class GridImpl final : public uf_grid {
     return copy_out(dst, ptr, lx, ly, lz, pitch);
   }
 
+  // ------------------------------------------------- bulk field transfer
+  // Staging buffer of each field for uf_set_fields / uf_get_fields: a step
+  // scratch array (recomputed by every step) at least as large as the
+  // field's dense layout.
+  T* staging(int f) {
+    switch (f) {
+      case UF_FIELD_U: return uh;
+      case UF_FIELD_V: return vh;
+      case UF_FIELD_W: return wh;
+      case UF_FIELD_P: return ut;
+      case UF_FIELD_K: return vt;
+      case UF_FIELD_OMEGA: return wt;
+      case UF_FIELD_PHI: return u2;
+      case UF_FIELD_NUT: return v2;
+    }
+    return nullptr;
+  }
+  static bool on_device(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  }
+  uf_status repack(const T* src, T* dst, int lx, int rows, int pitch, int to_padded) {
+    const size_t n = (size_t)lx * rows;
+    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
+    uf::k_repack<T><<<blocks, 256, 0, stream>>>(src, dst, lx, rows, pitch, to_padded);
+    UF_CUDA(cudaGetLastError());
+    return UF_OK;
+  }
+
+  uf_status set_fields(int n, const int* fields, const void* const* bufs) override {
+    if (n < 0 || (n > 0 && (!fields || !bufs))) return fail(UF_ERR_ARG, "NULL field list");
+    bool state = false;
+    for (int q = 0; q < n; ++q) {
+      T* ptr; int lx, ly, lz, pitch;
+      if (!field_geom(fields[q], &ptr, &lx, &ly, &lz, &pitch)) return fail(UF_ERR_ARG, "unknown field");
+      if (!bufs[q]) return fail(UF_ERR_ARG, "NULL buffer");
+    }
+    // every host copy first, back to back on the copy engine, then the repacks
+    for (int q = 0; q < n; ++q) {
+      T* ptr; int lx, ly, lz, pitch;
+      field_geom(fields[q], &ptr, &lx, &ly, &lz, &pitch);
+      if (!on_device(bufs[q]))
+        UF_CUDA(cudaMemcpyAsync(staging(fields[q]), bufs[q], (size_t)lx * ly * lz * sizeof(T), cudaMemcpyHostToDevice,
+                                stream));
+    }
+    for (int q = 0; q < n; ++q) {
+      T* ptr; int lx, ly, lz, pitch;
+      field_geom(fields[q], &ptr, &lx, &ly, &lz, &pitch);
+      T* dst = fields[q] == UF_FIELD_PHI ? phi : ptr;
+      const T* src = on_device(bufs[q]) ? reinterpret_cast<const T*>(bufs[q]) : staging(fields[q]);
+      uf_status s = repack(src, dst, lx, ly * lz, pitch, 1);
+      if (s != UF_OK) return s;
+      if (fields[q] == UF_FIELD_PHI) {
+        uf::k_drag_coeff<T><<<(unsigned)((P.n_c + 255) / 256), 256, 0, stream>>>(phi, cc, P.n_c, d.Cd, d.a, d.b, d.e);
+        UF_CUDA(cudaGetLastError());
+      }
+      state |= fields[q] == UF_FIELD_U || fields[q] == UF_FIELD_V || fields[q] == UF_FIELD_W;
+    }
+    if (state) have_state = true;
+    return UF_OK;
+  }
+
+  uf_status get_fields(int n, const int* fields, void* const* bufs) override {
+    if (n < 0 || (n > 0 && (!fields || !bufs))) return fail(UF_ERR_ARG, "NULL field list");
+    for (int q = 0; q < n; ++q) {
+      T* ptr; int lx, ly, lz, pitch;
+      if (!field_geom(fields[q], &ptr, &lx, &ly, &lz, &pitch)) return fail(UF_ERR_ARG, "unknown field");
+      if (!bufs[q]) return fail(UF_ERR_ARG, "NULL buffer");
+    }
+    // every repack first, then the host copies back to back
+    for (int q = 0; q < n; ++q) {
+      T* ptr; int lx, ly, lz, pitch;
+      field_geom(fields[q], &ptr, &lx, &ly, &lz, &pitch);
+      T* dst = on_device(bufs[q]) ? reinterpret_cast<T*>(bufs[q]) : staging(fields[q]);
+      uf_status s = repack(ptr, dst, lx, ly * lz, pitch, 0);
+      if (s != UF_OK) return s;
+    }
+    for (int q = 0; q < n; ++q) {
+      T* ptr; int lx, ly, lz, pitch;
+      field_geom(fields[q], &ptr, &lx, &ly, &lz, &pitch);
+      if (!on_device(bufs[q]))
+        UF_CUDA(cudaMemcpyAsync(bufs[q], staging(fields[q]), (size_t)lx * ly * lz * sizeof(T), cudaMemcpyDeviceToHost,
+                                stream));
+    }
+    UF_CUDA(cudaStreamSynchronize(stream));
+    return UF_OK;
+  }
+
   uf_status init_state() override {
     if (!init_exec) {
       int nf, ns, ni;
@@ -1622,6 +1714,14 @@ uf_status uf_adjoint_run(uf_grid* g, void* ws, size_t bytes, int nsteps, int ckp
                          double u_hi, double u_lo, void* dJ_dphi, double* J_out) {
   UF_NEED(g);
   return g->adjoint_run(ws, bytes, nsteps, ckpt_every, z_lo, z_hi, u_hi, u_lo, dJ_dphi, J_out);
+}
+uf_status uf_set_fields(uf_grid* g, int n, const int* fields, const void* const* bufs) {
+  UF_NEED(g);
+  return g->set_fields(n, fields, bufs);
+}
+uf_status uf_get_fields(uf_grid* g, int n, const int* fields, void* const* bufs) {
+  UF_NEED(g);
+  return g->get_fields(n, fields, bufs);
 }
 uf_status uf_step_vjp(uf_grid* g, void* d_ws, size_t bytes, const void* const* lam_out, void* const* lam_in,
                       void* lam_phi) {

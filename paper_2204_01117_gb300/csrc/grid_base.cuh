@@ -41,6 +41,8 @@ struct uf_grid {
   virtual uf_status set_porosity(const void*) = 0;
   virtual uf_status set_state(int, const void*) = 0;
   virtual uf_status get_state(int, void*) = 0;
+  virtual uf_status set_fields(int, const int*, const void* const*) = 0;
+  virtual uf_status get_fields(int, const int*, void* const*) = 0;
   virtual uf_status init_state() = 0;
   virtual uf_status step(uf_step_stats*) = 0;
   virtual uf_status run(int, uf_step_stats*) = 0;

@@ -667,4 +667,18 @@ __global__ void k_drag_coeff(const T* __restrict__ phi, T* __restrict__ cc, size
   cc[q] = (T)(Cd * a * pow(ratio, b));
 }
 
+// Dense <-> padded layout of one field (lx values per row, ly * lz rows; the
+// padded rows have pitch P).  to_padded: dst[r P + i] = src[r lx + i], else
+// the reverse.
+template <typename T>
+__global__ void __launch_bounds__(256) k_repack(const T* __restrict__ src, T* __restrict__ dst, int lx, int rows,
+                                                int P, int to_padded) {
+  const size_t n = (size_t)lx * rows;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = e / lx, i = e - r * lx;
+    if (to_padded) dst[r * P + i] = src[e];
+    else dst[e] = src[r * P + i];
+  }
+}
+
 }  // namespace uf

@@ -158,6 +158,10 @@ def load():
     lib.uf_adjoint_workspace_bytes.restype = ctypes.c_size_t
     lib.uf_adjoint_run.argtypes = [vp, vp, ctypes.c_size_t, ip, ip, dp, dp, dp, dp, vp, P(dp)]
     lib.uf_adjoint_run.restype = ip
+    lib.uf_set_fields.argtypes = [vp, ip, P(ip), P(vp)]
+    lib.uf_set_fields.restype = ip
+    lib.uf_get_fields.argtypes = [vp, ip, P(ip), P(vp)]
+    lib.uf_get_fields.restype = ip
     lib.uf_step_vjp.argtypes = [vp, vp, ctypes.c_size_t, P(vp), P(vp), vp]
     lib.uf_step_vjp.restype = ip
     lib.uf_design_to_phi.argtypes = [vp, ip, P(dp), P(dp), dp, vp]
@@ -531,6 +535,32 @@ class Grid:
 
     def launches_last_step(self) -> int:
         return int(self.lib.uf_last_step_launches(self._h))
+
+    def put_fields(self, bufs: dict) -> None:
+        """uf_set_fields: {name: array or tensor} in one call (dense layout)."""
+        names = list(bufs)
+        fl = (ctypes.c_int * len(names))(*[FIELDS[n] for n in names])
+        ptrs = (ctypes.c_void_p * len(names))()
+        keep = []
+        for q, n in enumerate(names):
+            p, k = self._arg(bufs[n])
+            ptrs[q] = p
+            keep.append(k)
+        check(self.lib.uf_set_fields(self._h, len(names), fl, ptrs))
+        self._keep_put = keep   # pinned buffers must outlive the enqueued copies
+
+    def take_fields(self, outs: dict) -> dict:
+        """uf_get_fields into {name: preallocated array or tensor}; one sync."""
+        names = list(outs)
+        fl = (ctypes.c_int * len(names))(*[FIELDS[n] for n in names])
+        ptrs = (ctypes.c_void_p * len(names))()
+        keep = []
+        for q, n in enumerate(names):
+            p, k = self._arg(outs[n])
+            ptrs[q] = p
+            keep.append(k)
+        check(self.lib.uf_get_fields(self._h, len(names), fl, ptrs))
+        return outs
 
     def state(self) -> dict:
         return {n: self.get_state(n) for n in ("u", "v", "w", "p", "k", "omega")}

@@ -269,3 +269,36 @@ def test_small_workspace_rejected():
     h = ctypes.c_void_p()
     assert lib.uf_create_grid(ctypes.byref(d), ctypes.c_void_p(ws.data_ptr()), need - 4096,
                               ctypes.c_void_p(s.cuda_stream), ctypes.byref(h)) == uf.UF_ERR_NOMEM
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_bulk_field_transfer_round_trip(precision):
+    """uf_set_fields / uf_get_fields (staged contiguous copies + repack
+    kernel) against uf_set_state / uf_get_state, host and device buffers,
+    on a ragged grid."""
+    import torch
+    nx, ny, nz = 45, 37, 11
+    g = uf.Grid(nx, ny, nz, precision=precision, wind_dir_deg=30.0)
+    f = layouts.random_fields(nx, ny, nz, seed=5)
+    host = {n: f[n].astype(g.np_dtype) for n in ("u", "v", "w", "p", "k", "omega")}
+    host["phi"] = np.random.default_rng(6).random((nz, ny, nx)).astype(g.np_dtype)
+    g.put_fields(host)
+    for n, a in host.items():
+        np.testing.assert_array_equal(g.get_state(n), a, err_msg=n)
+    out = g.take_fields({n: np.empty_like(a) for n, a in host.items()})
+    for n, a in host.items():
+        np.testing.assert_array_equal(out[n], a, err_msg=n)
+    # device tensors in both directions, after a step
+    g.step()
+    dev = {n: torch.empty(g.shapes[n], dtype=g.torch_dtype, device="cuda") for n in host}
+    g.take_fields(dev)
+    for n in host:
+        np.testing.assert_array_equal(dev[n].cpu().numpy(), g.get_state(n), err_msg=n)
+    g2 = uf.Grid(nx, ny, nz, precision=precision, wind_dir_deg=30.0)
+    g2.put_fields(dev)
+    torch.cuda.synchronize()
+    for n in host:
+        np.testing.assert_array_equal(g2.get_state(n), g.get_state(n), err_msg=n)
+    fl = (ctypes.c_int * 1)(uf.FIELDS["u"])
+    assert g.lib.uf_set_fields(g._h, 1, fl, (ctypes.c_void_p * 1)(None)) == uf.UF_ERR_ARG
+    assert g.lib.uf_get_fields(g._h, 1, (ctypes.c_int * 1)(99), (ctypes.c_void_p * 1)(1)) == uf.UF_ERR_ARG
