@@ -161,7 +161,7 @@ template <typename T>
 struct RhsP {
   uf::StepParams<T> sp;
   const T *u, *v, *w;
-  T* b;
+  T *b, *pr, *pp;
   double* partials;
   uf::SolveState* st;
 };
@@ -239,7 +239,7 @@ template <typename T>
 __global__ void __launch_bounds__(uf::NT, 6) kb_pressure_rhs(const __grid_constant__ Args<RhsP<T>> A) {
   for_items(&A.m, [&](int i, int zc, const VBlock& vb) {
     const RhsP<T>& P = A.at[i];
-    uf::pressure_rhs_body<T>(P.sp, P.u, P.v, P.w, P.b, zc, P.partials, P.st, vb);
+    uf::pressure_rhs_body<T>(P.sp, P.u, P.v, P.w, P.b, P.pr, P.pp, zc, P.partials, P.st, vb);
   });
 }
 
@@ -663,10 +663,12 @@ class BatchImpl final : public uf_batch {
         P.sp = G.sp;
         P.u = G.u; P.v = G.v; P.w = G.w;
         P.b = G.b;
+        P.pr = G.p;
+        P.pp = G.pp;
         P.partials = G.partials;
         P.st = G.st;
       });
-      L(s, "b_pressure_rhs", plane_bytes(MAP_CHUNK, 4),
+      L(s, "b_pressure_rhs", plane_bytes(MAP_CHUNK, 8),
         [&] { k<<<grid_of(k, uf::NT, 0, items(MAP_CHUNK)), blk, 0, s>>>(A); });
     }
     L(s, "b_begin_solve", 0, [&] { kb_begin_solve<<<1, 32, 0, s>>>(d_left, n); });

@@ -116,7 +116,7 @@ struct Plan {
   std::vector<LevelDims> levels;
   int coarse_n;
   // offsets
-  size_t u, v, w, uh, vh, wh, ut, vt, wt, u2, v2, w2, k0, k1, o0, o1, cc, phi, nut, p, b, r, r2, z, q, d0, d1;
+  size_t u, v, w, uh, vh, wh, ut, vt, wt, u2, v2, w2, k0, k1, o0, o1, cc, phi, nut, p, pp, b, r, r2, z, q, d0, d1;
   int nl;                  // multigrid levels in use (1 without MG)
   int auto_tail_level;     // shallowest level whose tail fits the shared-memory budget
   int tail_level;          // first level run by the shared-memory tail kernel
@@ -146,7 +146,7 @@ Plan make_plan(const uf_grid_desc* d) {
   P.k0 = L.take(P.n_c * tb); P.k1 = L.take(P.n_c * tb);
   P.o0 = L.take(P.n_c * tb); P.o1 = L.take(P.n_c * tb);
   P.cc = L.take(P.n_c * tb); P.phi = L.take(P.n_c * tb); P.nut = L.take(P.n_c * tb);
-  P.p = L.take(P.n_c * tb); P.b = L.take(P.n_c * tb); P.r = L.take(P.n_c * tb);
+  P.p = L.take(P.n_c * tb); P.pp = L.take(P.n_c * tb); P.b = L.take(P.n_c * tb); P.r = L.take(P.n_c * tb);
   P.r2 = L.take(P.n_c * tb);
   P.z = L.take(P.n_c * tb); P.q = L.take(P.n_c * tb);
   P.d0 = L.take(P.n_c * tb); P.d1 = L.take(P.n_c * tb);
@@ -303,7 +303,8 @@ class GridImpl final : public uf_grid {
   cudaStream_t stream = nullptr, cap = nullptr, cap2 = nullptr;
   uf::StepParams<T> sp;
   std::vector<uf::Level<T>> lv;
-  T *u, *v, *w, *uh, *vh, *wh, *ut, *vt, *wt, *u2, *v2, *w2, *kb[2], *ob[2], *cc, *phi, *nut, *p, *b, *r, *r2, *z, *q, *d0, *d1, *prof;
+  T *u, *v, *w, *uh, *vh, *wh, *ut, *vt, *wt, *u2, *v2, *w2, *kb[2], *ob[2], *cc, *phi, *nut, *p, *pp, *b, *r, *r2, *z, *q,
+    *d0, *d1, *prof;
   uf::TailArgs<T> tail;
   T* sol_x = nullptr;   // the solve's unknown (p for the step; mu for the adjoint)
   T* sol_b = nullptr;   // its right-hand side
@@ -341,7 +342,7 @@ class GridImpl final : public uf_grid {
     ut = at<T>(P.ut); vt = at<T>(P.vt); wt = at<T>(P.wt);
     u2 = at<T>(P.u2); v2 = at<T>(P.v2); w2 = at<T>(P.w2);
     kb[0] = at<T>(P.k0); kb[1] = at<T>(P.k1); ob[0] = at<T>(P.o0); ob[1] = at<T>(P.o1);
-    cc = at<T>(P.cc); phi = at<T>(P.phi); nut = at<T>(P.nut); p = at<T>(P.p); b = at<T>(P.b);
+    cc = at<T>(P.cc); phi = at<T>(P.phi); nut = at<T>(P.nut); p = at<T>(P.p); pp = at<T>(P.pp); b = at<T>(P.b);
     sol_x = p;
     sol_b = b;
     r = at<T>(P.r); r2 = at<T>(P.r2); z = at<T>(P.z); q = at<T>(P.q); d0 = at<T>(P.d0); d1 = at<T>(P.d1);
@@ -697,7 +698,8 @@ class GridImpl final : public uf_grid {
     L(s, "drag_bc", 2 * faces + cells, [&] { uf::k_drag_bc<T><<<ga, blk, 0, s>>>(sp, u2, v2, w2, cc, u, v, w); });
     int zc;
     const dim3 gr = chunk_grid(d.nx, d.ny, d.nz, &zc);
-    L(s, "pressure_rhs", faces + cells, [&] { uf::k_pressure_rhs<T><<<gr, blk, 0, s>>>(sp, u, v, w, b, zc, partials, st); });
+    L(s, "pressure_rhs", faces + 5 * cells,
+      [&] { uf::k_pressure_rhs<T><<<gr, blk, 0, s>>>(sp, u, v, w, b, p, pp, zc, partials, st); });
   }
 
   void rec_post(cudaStream_t s, const T* kin, const T* oin, T* kout, T* oout) {
@@ -758,7 +760,7 @@ class GridImpl final : public uf_grid {
     int C, nseg;
     size_t tape0, ckpt0, fin, lam;
     // offsets inside one tape slot; a slot starts with a checkpoint
-    // (faces | k | omega | p) so that save_state() fills its head
+    // (faces | k | omega | p | previous p) so that save_state() fills its head
     size_t s_nut, s_uh, s_ut, s_u2, s_u1;
   };
   static size_t a64(size_t n) { return (n + 63) / 64 * 64; }
@@ -769,7 +771,7 @@ class GridImpl final : public uf_grid {
     A.cellN = a64(P.n_c);
     A.C = C;
     A.nseg = (nsteps + C - 1) / C;
-    A.ckpt = A.faceN + 3 * A.cellN;       // faces, k, omega, p
+    A.ckpt = A.faceN + 4 * A.cellN;       // faces, k, omega, p, p of the previous step
     A.s_nut = A.ckpt;
     A.s_uh = A.s_nut + A.cellN;
     A.s_ut = A.s_uh + A.faceN;
@@ -806,13 +808,14 @@ class GridImpl final : public uf_grid {
   cudaError_t copy_cell(T* dst, const T* src) {
     return cudaMemcpyAsync(dst, src, P.n_c * sizeof(T), cudaMemcpyDeviceToDevice, stream);
   }
-  // checkpoint layout: faces | k | omega | p
+  // checkpoint layout: faces | k | omega | p | previous p (the solve's extrapolation)
   cudaError_t save_state(T* slot, const AdjLayout& A) {
     FaceSet f = faces_at(slot);
     cudaError_t e = copy_faces(f, u, v, w);
     if (e == cudaSuccess) e = copy_cell(slot + A.faceN, kb[parity]);
     if (e == cudaSuccess) e = copy_cell(slot + A.faceN + A.cellN, ob[parity]);
     if (e == cudaSuccess) e = copy_cell(slot + A.faceN + 2 * A.cellN, p);
+    if (e == cudaSuccess) e = copy_cell(slot + A.faceN + 3 * A.cellN, pp);
     return e;
   }
   cudaError_t load_state(const T* slot, const AdjLayout& A) {
@@ -824,6 +827,7 @@ class GridImpl final : public uf_grid {
     if (e == cudaSuccess) e = copy_cell(kb[0], slot + A.faceN);
     if (e == cudaSuccess) e = copy_cell(ob[0], slot + A.faceN + A.cellN);
     if (e == cudaSuccess) e = copy_cell(p, slot + A.faceN + 2 * A.cellN);
+    if (e == cudaSuccess) e = copy_cell(pp, slot + A.faceN + 3 * A.cellN);
     return e;
   }
 
@@ -1281,7 +1285,7 @@ class GridImpl final : public uf_grid {
     V.sp = sp;
     V.adv = advect_args();
     V.u = u; V.v = v; V.w = w; V.uh = uh; V.vh = vh; V.wh = wh; V.ut = ut; V.vt = vt; V.wt = wt;
-    V.u2 = u2; V.v2 = v2; V.w2 = w2; V.cc = cc; V.nut = nut; V.p = p; V.b = b; V.z = z; V.q = q;
+    V.u2 = u2; V.v2 = v2; V.w2 = w2; V.cc = cc; V.nut = nut; V.p = p; V.pp = pp; V.b = b; V.z = z; V.q = q;
     V.d0 = d0; V.d1 = d1;
     V.kb[0] = kb[0]; V.kb[1] = kb[1]; V.ob[0] = ob[0]; V.ob[1] = ob[1];
     V.parity = parity;
@@ -1355,6 +1359,7 @@ class GridImpl final : public uf_grid {
     if (f == UF_FIELD_PHI) return set_porosity(src);
     uf_status s = copy_in(ptr, lx, ly, lz, pitch, src);
     if (s == UF_OK && (f == UF_FIELD_U || f == UF_FIELD_V || f == UF_FIELD_W)) have_state = true;
+    if (s == UF_OK && f == UF_FIELD_P) UF_CUDA(copy_cell(pp, p));   // a new pressure has no history
     return s;
   }
 
@@ -1425,6 +1430,7 @@ class GridImpl final : public uf_grid {
         UF_CUDA(cudaGetLastError());
       }
       state |= fields[q] == UF_FIELD_U || fields[q] == UF_FIELD_V || fields[q] == UF_FIELD_W;
+      if (fields[q] == UF_FIELD_P) UF_CUDA(copy_cell(pp, p));
     }
     if (state) have_state = true;
     return UF_OK;
@@ -1471,7 +1477,7 @@ class GridImpl final : public uf_grid {
         uf::k_drag_bc<T><<<ga, blk, 0, s>>>(sp, u, v, w, cc, uh, vh, wh);
         int zc;
         const dim3 gr = chunk_grid(d.nx, d.ny, d.nz, &zc);
-        uf::k_pressure_rhs<T><<<gr, blk, 0, s>>>(sp, uh, vh, wh, b, zc, partials, st);
+        uf::k_pressure_rhs<T><<<gr, blk, 0, s>>>(sp, uh, vh, wh, b, nullptr, nullptr, zc, partials, st);
         rec_count += 2;
       };
       auto post = [&](cudaStream_t s) {
@@ -1487,6 +1493,7 @@ class GridImpl final : public uf_grid {
     }
     parity = 0;
     UF_CUDA(cudaGraphLaunch(init_exec, stream));
+    UF_CUDA(copy_cell(pp, p));   // no previous pressure: the first guess is p itself
     have_state = true;
     return check_device(nullptr);
   }
@@ -1596,6 +1603,7 @@ class GridImpl final : public uf_grid {
       if (s != UF_OK) return s;
     }
     UF_CUDA(cudaGraphLaunch(solve_exec, stream));
+    UF_CUDA(copy_cell(pp, p));
     uf_step_stats o;
     s = check_device(&o);
     if (iters) *iters = o.cg_iters;

@@ -414,9 +414,14 @@ struct SolveState {
 };
 
 template <typename T>
+// With pr != nullptr the kernel also forms the initial guess of the solve by
+// linear extrapolation in time, pr <- 2 p^n - p^{n-1}, keeping p^n in pp as
+// the next step's p^{n-1}; only the starting point of CG changes, not the
+// solution it converges to.
 __device__ __forceinline__ void pressure_rhs_body(const StepParams<T>& p, const T* __restrict__ u,
                                                   const T* __restrict__ v, const T* __restrict__ w, T* __restrict__ b,
-                                                  int zc, double* partials, SolveState* st, const VBlock& vb) {
+                                                  T* __restrict__ pr, T* __restrict__ pp, int zc, double* partials,
+                                                  SolveState* st, const VBlock& vb) {
   __shared__ double sh[32];
   __shared__ bool last;
   const int i = vb.x * BX + threadIdx.x, j = vb.y * BY + threadIdx.y;
@@ -427,8 +432,14 @@ __device__ __forceinline__ void pressure_rhs_body(const StepParams<T>& p, const 
     const T sc = -p.rho * p.h / *p.dtT;
     for (int k = z0; k < z1; ++k) {
       const T bv = sc * cell_flux(p, u, v, w, i, j, k);
-      b[idx_c(p, i, j, k)] = bv;
+      const size_t c = idx_c(p, i, j, k);
+      b[c] = bv;
       dacc.add(bv, bv);
+      if (pr) {
+        const T pn = pr[c];
+        pr[c] = T(2) * pn - pp[c];
+        pp[c] = pn;
+      }
     }
   }
   acc += dacc.value();
@@ -449,9 +460,9 @@ __device__ __forceinline__ void pressure_rhs_body(const StepParams<T>& p, const 
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_pressure_rhs(StepParams<T> p, const T* __restrict__ u, const T* __restrict__ v,
-                                                     const T* __restrict__ w, T* __restrict__ b, int zc,
-                                                     double* partials, SolveState* st) {
-  pressure_rhs_body<T>(p, u, v, w, b, zc, partials, st, vblock());
+                                                     const T* __restrict__ w, T* __restrict__ b, T* __restrict__ pr,
+                                                     T* __restrict__ pp, int zc, double* partials, SolveState* st) {
+  pressure_rhs_body<T>(p, u, v, w, b, pr, pp, zc, partials, st, vblock());
 }
 
 
