@@ -241,10 +241,13 @@ __global__ void __launch_bounds__(NT) k_turbulence_adj(StepParams<T> p, const T*
 // u1 = u3 + G A^-1 Dv u3 (projection with its scaling), so
 // lambda_u3 = lambda + Dv^T mu with A mu = G^T lambda.
 // k_proj_adj_rhs: b(c) = G^T lambda: + lambda on the low face of c, - on
-// the high face, projected faces only.
+// the high face, projected faces only.  It also sets the initial guess of
+// the solve, mu <- 2 mu - mu_prev (linear extrapolation along the reverse
+// sweep, as for the forward pressure), keeping mu in mu_prev.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_proj_adj_rhs(StepParams<T> p, const T* __restrict__ lu, const T* __restrict__ lv,
-                                                     const T* __restrict__ lw, T* __restrict__ b) {
+                                                     const T* __restrict__ lw, T* __restrict__ b, T* __restrict__ mu,
+                                                     T* __restrict__ mu_prev) {
   const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= p.nx || j >= p.ny) return;
   auto proj_u = [&](int ii) { return (ii > 0 && ii < p.nx) || (ii == 0 && p.side[0] == OUTFLOW) || (ii == p.nx && p.side[1] == OUTFLOW); };
@@ -257,7 +260,11 @@ __global__ void __launch_bounds__(NT) k_proj_adj_rhs(StepParams<T> p, const T* _
   if (proj_v(j + 1)) s -= lv[idx_v(p, i, j + 1, k)];
   if (proj_w(k)) s += lw[idx_c(p, i, j, k)];
   if (proj_w(k + 1)) s -= lw[idx_c(p, i, j, k + 1)];
-  b[idx_c(p, i, j, k)] = s;
+  const size_t c = idx_c(p, i, j, k);
+  b[c] = s;
+  const T m = mu[c];
+  mu[c] = T(2) * m - mu_prev[c];
+  mu_prev[c] = m;
 }
 
 // lambda(f) += mu(c-) - mu(c+) on every face (missing cells count 0).
@@ -569,7 +576,7 @@ struct AdvectAdj {
 
 // Pass A: transpose of the backward step, correction and clamp.
 template <typename T>
-__global__ void __launch_bounds__(NT) k_advect_backward_adj(AdvectArgs<T> A, AdvectAdj<T> J) {
+__global__ void __launch_bounds__(NT, 2) k_advect_backward_adj(AdvectArgs<T> A, AdvectAdj<T> J) {
   int q, k;
   plane_of(blockIdx.z, A.nz, q, k);
   const Lattice L = q == 0 ? A.Lu : (q == 1 ? A.Lv : A.Lw);

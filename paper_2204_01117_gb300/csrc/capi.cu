@@ -782,7 +782,7 @@ class GridImpl final : public uf_grid {
     A.ckpt0 = A.tape0 + (size_t)C * A.slot;
     A.fin = A.ckpt0 + (size_t)A.nseg * A.ckpt;
     A.lam = A.fin + A.ckpt;
-    A.total = A.lam + 5 * A.faceN + 9 * A.cellN;
+    A.total = A.lam + 5 * A.faceN + 10 * A.cellN;
     return A;
   }
   size_t adjoint_bytes(int nsteps, int C) override {
@@ -838,7 +838,7 @@ class GridImpl final : public uf_grid {
   // Adjoint arrays inside the workspace (after the tapes and checkpoints).
   struct AdjArrays {
     FaceSet L0, L1, Lt, L2, Lh;   // adjoints: step input, step output, advected, diffused, forward SL
-    T *lk0, *lk1, *lo0, *lo1, *lnut, *lc, *mu, *badj, *lphi;
+    T *lk0, *lk1, *lo0, *lo1, *lnut, *lc, *mu, *badj, *lphi, *mu_prev;
   };
   AdjArrays adj_arrays(T* base, const AdjLayout& A) const {
     AdjArrays R;
@@ -851,7 +851,7 @@ class GridImpl final : public uf_grid {
     T* cells = lam + 5 * A.faceN;
     R.lk0 = cells; R.lk1 = cells + A.cellN; R.lo0 = cells + 2 * A.cellN; R.lo1 = cells + 3 * A.cellN;
     R.lnut = cells + 4 * A.cellN; R.lc = cells + 5 * A.cellN; R.mu = cells + 6 * A.cellN;
-    R.badj = cells + 7 * A.cellN; R.lphi = cells + 8 * A.cellN;
+    R.badj = cells + 7 * A.cellN; R.lphi = cells + 8 * A.cellN; R.mu_prev = cells + 9 * A.cellN;
     return R;
   }
 
@@ -917,7 +917,7 @@ class GridImpl final : public uf_grid {
     uf::k_turbulence_adj<T><<<gc, blk, 0, stream>>>(sp, U1.u, U1.v, U1.w, K0, O0, R.lk1, R.lo1, R.lk0, R.lo0, R.L1.u,
                                                     R.L1.v, R.L1.w);
     // a8^T: projection (A symmetric: the same MG-PCG)
-    uf::k_proj_adj_rhs<T><<<gc, blk, 0, stream>>>(sp, R.L1.u, R.L1.v, R.L1.w, R.badj);
+    uf::k_proj_adj_rhs<T><<<gc, blk, 0, stream>>>(sp, R.L1.u, R.L1.v, R.L1.w, R.badj, R.mu, R.mu_prev);
     UF_CUDA(cudaGraphLaunch(adj_solve_exec, stream));
     uf::k_proj_adj_apply<T><<<ga, blk, 0, stream>>>(sp, R.mu, R.L1.u, R.L1.v, R.L1.w);
     // a4/a5^T: drag and velocity BCs
@@ -953,12 +953,19 @@ class GridImpl final : public uf_grid {
     AdjArrays R = adj_arrays(base, A);
     s = ensure_adj_solve(R.mu, R.badj);
     if (s != UF_OK) return s;
-    UF_CUDA(cudaMemsetAsync(base + A.lam, 0, (5 * A.faceN + 9 * A.cellN) * sizeof(T), stream));
-    // 1. forward sweep with checkpoints every C steps
+    UF_CUDA(cudaMemsetAsync(base + A.lam, 0, (5 * A.faceN + 10 * A.cellN) * sizeof(T), stream));
+    // 1. forward sweep with checkpoints every C steps; the last segment is
+    //    taped on the way, so the reverse sweep need not recompute it
+    const int last0 = (A.nseg - 1) * C;
     for (int n = 0; n < nsteps; ++n) {
       if (n % C == 0) UF_CUDA(save_state(base + A.ckpt0 + (size_t)(n / C) * A.ckpt, A));
-      UF_CUDA(cudaGraphLaunch(step_exec[parity], stream));
-      parity ^= 1;
+      if (n >= last0) {
+        s = tape_step(base + A.tape0 + (size_t)(n - last0) * A.slot, A);
+        if (s != UF_OK) return s;
+      } else {
+        UF_CUDA(cudaGraphLaunch(step_exec[parity], stream));
+        parity ^= 1;
+      }
     }
     UF_CUDA(save_state(base + A.fin, A));
     s = check_device(nullptr);
@@ -981,10 +988,12 @@ class GridImpl final : public uf_grid {
     // 3. reverse sweep, one checkpoint segment at a time
     for (int seg = A.nseg - 1; seg >= 0; --seg) {
       const int n0 = seg * C, n1 = std::min(nsteps, n0 + C);
-      UF_CUDA(load_state(base + A.ckpt0 + (size_t)seg * A.ckpt, A));
-      for (int n = n0; n < n1; ++n) {   // recompute the segment, taping each step
-        s = tape_step(base + A.tape0 + (size_t)(n - n0) * A.slot, A);
-        if (s != UF_OK) return s;
+      if (seg < A.nseg - 1) {
+        UF_CUDA(load_state(base + A.ckpt0 + (size_t)seg * A.ckpt, A));
+        for (int n = n0; n < n1; ++n) {   // recompute the segment, taping each step
+          s = tape_step(base + A.tape0 + (size_t)(n - n0) * A.slot, A);
+          if (s != UF_OK) return s;
+        }
       }
       for (int n = n1 - 1; n >= n0; --n) {
         s = reverse_step(base + A.tape0 + (size_t)(n - n0) * A.slot, A, R);
@@ -1023,7 +1032,7 @@ class GridImpl final : public uf_grid {
     AdjArrays R = adj_arrays(base, A);
     s = ensure_adj_solve(R.mu, R.badj);
     if (s != UF_OK) return s;
-    UF_CUDA(cudaMemsetAsync(base + A.lam, 0, (5 * A.faceN + 9 * A.cellN) * sizeof(T), stream));
+    UF_CUDA(cudaMemsetAsync(base + A.lam, 0, (5 * A.faceN + 10 * A.cellN) * sizeof(T), stream));
     T* keep = base + A.ckpt0;
     UF_CUDA(save_state(keep, A));
     T* t = base + A.tape0;
