@@ -121,6 +121,7 @@ struct Plan {
   int auto_tail_level;     // shallowest level whose tail fits the shared-memory budget
   int tail_level;          // first level run by the shared-memory tail kernel
   size_t tail_smem;        // its dynamic shared memory (bytes)
+  size_t tail_cr_off;      // byte offset of the coarsest solve's FP64 right-hand side in it
   std::vector<int> tail_off;
   std::vector<size_t> lr, lx, lt;
   size_t prof, dt, dtT, scal, state, partials, ainv, boxes, grad;
@@ -192,7 +193,7 @@ size_t tail_bytes(const Plan& P, int lt) {
   size_t n = 0;
   for (int m = lt; m < P.nl; ++m)
     n += 3 * (size_t)(P.levels[m].nx + 2) * (P.levels[m].ny + 2) * (P.levels[m].nz + 2);
-  return n * P.T_bytes;
+  return round_up(n * P.T_bytes, 16) + sizeof(double) * (size_t)P.coarse_n;
 }
 
 void plan_tail(Plan& P, int lt) {
@@ -207,7 +208,9 @@ void plan_tail(Plan& P, int lt) {
     P.tail_off[m] = (int)off;
     off += 3 * (size_t)(P.levels[m].nx + 2) * (P.levels[m].ny + 2) * (P.levels[m].nz + 2);
   }
-  P.tail_smem = off * P.T_bytes;
+  // then the compact FP64 right-hand side of the coarsest solve
+  P.tail_cr_off = round_up(off * P.T_bytes, 16);
+  P.tail_smem = P.tail_cr_off + sizeof(double) * (size_t)P.coarse_n;
 }
 
 // Dense operator of a level (compact order i + nx (j + ny k)).
@@ -417,6 +420,7 @@ class GridImpl final : public uf_grid {
       if (nl > uf::MAX_LEVELS) return fail(UF_ERR_ARG, "too many multigrid levels");
       for (size_t l = 0; l < nl; ++l) { tail.lv[l] = lv[l]; tail.off[l] = P.tail_off[l]; }
       tail.lt = P.tail_level;
+      tail.cr_off = (int)P.tail_cr_off;
       tail.nl = (int)nl;
       tail.ainv = ainv;
       tail.n_coarse = P.coarse_n;
@@ -1173,6 +1177,7 @@ class GridImpl final : public uf_grid {
     plan_tail(P, lt);
     for (int l = 0; l < P.nl; ++l) tail.off[l] = P.tail_off[l];
     tail.lt = lt;
+    tail.cr_off = (int)P.tail_cr_off;
     UF_CUDA(set_smem_limits());
     return UF_OK;
   }

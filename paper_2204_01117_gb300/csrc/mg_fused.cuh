@@ -518,6 +518,7 @@ struct TailArgs {
   Level<T> lv[MAX_LEVELS];
   int lt, nl;
   int off[MAX_LEVELS];   // element offset of each tail level's three bordered arrays
+  int cr_off;            // byte offset of the compact FP64 right-hand side of the coarsest solve
   const double* ainv;
   int n_coarse;
 };
@@ -597,7 +598,10 @@ __device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, const SmoothW
     }
     __syncthreads();
   }
-  // coarsest level: a = A^-1 r (FP64 dense inverse), one warp per row
+  // coarsest level: a = A^-1 r with the FP64 dense inverse.  r is first
+  // copied into a compact FP64 vector placed after the tail's arrays; then
+  // groups of 8 lanes take a row each, every lane a stride-8 set of columns,
+  // and the group's partial sums meet by shuffles.
   {
     const int m = A.nl - 1;
     const Level<T>& L = A.lv[m];
@@ -605,18 +609,26 @@ __device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, const SmoothW
     geom(m, X, P, NB);
     const T* r = S + A.off[m];
     T* a = S + A.off[m] + NB;
-    const int n = A.n_coarse, warp = tid >> 5, lane = tid & 31;
-    for (int row = warp; row < n; row += TAIL_T / 32) {
-      double s = 0.0;
-      for (int c = lane; c < n; c += 32) {
-        const int i = c % L.nx, j = (c / L.nx) % L.ny, k = c / (L.nx * L.ny);
-        s += A.ainv[(size_t)row * n + c] * (double)r[(i + 1) + X * (j + 1) + P * (k + 1)];
+    const int n = A.n_coarse;
+    double* cr = reinterpret_cast<double*>(smem_raw + A.cr_off);
+    for (int c = tid; c < n; c += TAIL_T) {
+      const int i = c % L.nx, j = (c / L.nx) % L.ny, k = c / (L.nx * L.ny);
+      cr[c] = (double)r[(i + 1) + X * (j + 1) + P * (k + 1)];
+    }
+    __syncthreads();
+    constexpr int G = 8;
+    const int lane = tid % G;
+    for (int row = tid / G; row < ((n + (TAIL_T / G) - 1) / (TAIL_T / G)) * (TAIL_T / G); row += TAIL_T / G) {
+      double sum = 0.0;
+      if (row < n) {
+        const double* arow = A.ainv + (size_t)row * n;
+        for (int c = lane; c < n; c += G) sum += arow[c] * cr[c];
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) {
+      for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (row < n && lane == 0) {
         const int i = row % L.nx, j = (row / L.nx) % L.ny, k = row / (L.nx * L.ny);
-        a[(i + 1) + X * (j + 1) + P * (k + 1)] = (T)s;
+        a[(i + 1) + X * (j + 1) + P * (k + 1)] = (T)sum;
       }
     }
   }
