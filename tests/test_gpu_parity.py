@@ -147,13 +147,13 @@ def test_single_box_fp64_100_steps_every_step():
     assert g.divergence() <= 1e-10
 
 
-def test_fp32_long_run_within_1e3():
+def test_fp32_500_steps_within_1e3_and_divergence_free():
     sc = layouts.urban_block(48, 40, 16, h=2.0, n_boxes=4, n_trees=6, seed=7, footprint=(6.0, 16.0),
                              height=(6.0, 20.0), radius=(2.0, 5.0), u_ref=3.0)
     o, g = pair(sc, "f32")
     o.init()
     g.init_state()
-    for n in range(300):
+    for n in range(499):
         g.step(stats=False)
         o.step()
     st = g.step()
@@ -162,6 +162,8 @@ def test_fp32_long_run_within_1e3():
     for f in FIELDS6:
         e = rel(g.get_state(f), o.get(f))
         assert e <= 1e-3, (f, e)
+    # projected divergence of the FP32 run, ||h div u|| / ||u_c||
+    assert g.divergence() <= 1e-6
 
 
 @pytest.mark.parametrize("precision", ["f32", "f64"])
