@@ -312,6 +312,45 @@ def batched_leg(steps: int = 10, peak: float = 6790.0, peak_kind: str = "measure
     }
 
 
+# ------------------------------------------------------ preconditioner table
+
+def preconditioner_table(steps: int = 10):
+    """CG iterations and step time on the 256x256x64 urban block for each
+    solver configuration: MG (three smoothers), the paper's AI1 / AI2, Jacobi
+    and plain CG under the residual stop rule (||r|| <= 1e-7 ||b||), and AI1 /
+    AI2 under the paper's rule (r.z <= 1e-5 ||b||^2, App. A.3), with the
+    divergence left after a step.  Each is timed with CUDA events over
+    `steps` steps after 3 warm-up steps from the same initial projection."""
+    import numpy as np
+    import torch
+    from paper_2204_01117_gb300 import layouts, uf
+    sc = layouts.urban_block(NX, NY, NZ, seed=0)
+    cases = [("mg", dict(precond="mg", mg_smoother="cheby")), ("mg-jacobi", dict(precond="mg", mg_smoother="jacobi")),
+             ("mg-rbgs", dict(precond="mg", mg_smoother="rbgs")), ("ai2", dict(precond="ai2")),
+             ("ai1", dict(precond="ai1")), ("jacobi", dict(precond="jacobi")), ("none", dict(precond="none")),
+             ("ai2-paper-rule", dict(precond="ai2", cg_stop_rule="paper")),
+             ("ai1-paper-rule", dict(precond="ai1", cg_stop_rule="paper"))]
+    rows = []
+    for name, kw in cases:
+        g = uf.Grid(sc.nx, sc.ny, sc.nz, precision="f32", cg_max_iter=5000, **kw, **sc.params())
+        g.set_porosity(sc.phi.astype(np.float32))
+        g.init_state()
+        g.run(3, stats=False)
+        st0 = g.step()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(g.stream)
+        g.run(steps, stats=False)
+        e1.record(g.stream)
+        torch.cuda.synchronize()
+        st1 = g.step()
+        its = (st1.cg_iters_total - st0.cg_iters_total - st1.cg_iters) / steps
+        rows.append({"solver": name, "ms_per_step": e0.elapsed_time(e1) / steps, "cg_iters_per_step": its,
+                     "divergence": g.divergence()})
+        g.close()
+    return {"workload": "urban block 256x256x64 FP32, " + str(steps) + " timed steps after 3", "rows": rows}
+
+
 # ---------------------------------------------------------------- oracle arm
 
 def oracle_sample(max_seconds: float = 150.0, steps_wanted: int = 1):
@@ -477,7 +516,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 32-instance leg")
+    ap.add_argument("--preconditioners", action="store_true",
+                    help="print the solver comparison table (CG iterations, step time) instead of the bench line")
     args = ap.parse_args()
+    if args.preconditioners:
+        import torch
+        torch.cuda.set_device(0)
+        from paper_2204_01117_gb300 import uf
+        uf.build()
+        uf.load()
+        print(json.dumps(preconditioner_table()), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

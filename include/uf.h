@@ -61,7 +61,13 @@ enum { UF_F32 = 0,   /* FP32 fields, FP64 reductions and coarsest MG solve */
 enum { UF_PRECOND_MG = 0,      /* geometric multigrid V-cycle (default)       */
        UF_PRECOND_AI1 = 1,     /* approximate inverse, 1st order (Sec. 3)     */
        UF_PRECOND_JACOBI = 2,
-       UF_PRECOND_NONE = 3 };
+       UF_PRECOND_NONE = 3,
+       UF_PRECOND_AI2 = 4 };   /* approximate inverse, 2nd order (Sec. 3)     */
+
+enum { UF_STOP_RESIDUAL = 0,   /* ||r|| <= cg_tol ||b|| (default)            */
+       UF_STOP_PAPER = 1 };    /* r.z <= cg_tol ||b||^2 with z = M^-1 r, the
+                                  rule of App. A.3 (cg_tol 1e-5 there); only
+                                  with the AI, Jacobi and no preconditioner  */
 
 enum { UF_FIELD_U = 0, UF_FIELD_V = 1, UF_FIELD_W = 2, UF_FIELD_P = 3,
        UF_FIELD_K = 4, UF_FIELD_OMEGA = 5, UF_FIELD_PHI = 6, UF_FIELD_NUT = 7 };
@@ -96,6 +102,7 @@ typedef struct {
   double mg_jacobi_omega;  /* damping of the MG Jacobi smoother (6/7)       */
   int mg_coarse_max;       /* coarsest MG level has at most this many cells */
   int mg_smoother;         /* UF_SMOOTH_CHEBY (default), _JACOBI or _RBGS   */
+  int cg_stop_rule;        /* UF_STOP_RESIDUAL (default) or UF_STOP_PAPER   */
 } uf_grid_desc;
 
 enum { UF_SMOOTH_JACOBI = 0,   /* damped Jacobi, 2 sweeps before + 2 after        */

@@ -87,7 +87,12 @@ bool desc_valid(const uf_grid_desc* d, std::string* why) {
   if (d->precision != UF_F32 && d->precision != UF_F64) { *why = "precision must be UF_F32 or UF_F64"; return false; }
   if (!(d->u_ref >= 0) || (d->u_ref == 0 && !(d->fixed_dt > 0))) { *why = "u_ref must be > 0 (or fixed_dt > 0)"; return false; }
   if (d->inflow_loglaw && !(d->z0 > 0 && d->z_ref > d->z0)) { *why = "log law needs z_ref > z0 > 0"; return false; }
-  if (d->precond < UF_PRECOND_MG || d->precond > UF_PRECOND_NONE) { *why = "unknown preconditioner"; return false; }
+  if (d->precond < UF_PRECOND_MG || d->precond > UF_PRECOND_AI2) { *why = "unknown preconditioner"; return false; }
+  if (d->cg_stop_rule != UF_STOP_RESIDUAL && d->cg_stop_rule != UF_STOP_PAPER) { *why = "unknown stop rule"; return false; }
+  if (d->cg_stop_rule == UF_STOP_PAPER && d->precond == UF_PRECOND_MG) {
+    *why = "the stop rule of App. A.3 needs the AI, Jacobi or no preconditioner";
+    return false;
+  }
   if (!(d->cg_tol >= 0) || d->cg_max_iter < 1) { *why = "cg_tol >= 0 and cg_max_iter >= 1 required"; return false; }
   if (d->mg_smoother != UF_SMOOTH_JACOBI && d->mg_smoother != UF_SMOOTH_RBGS && d->mg_smoother != UF_SMOOTH_CHEBY) {
     *why = "unknown smoother";
@@ -388,8 +393,11 @@ class GridImpl final : public uf_grid {
     // solver constants
     uf::SolveState s0;
     std::memset(&s0, 0, sizeof(s0));
-    const double tol = d.cg_tol > 0 ? d.cg_tol : (d.precision == UF_F64 ? 1e-12 : 1e-7);
-    s0.tol2 = tol * tol;
+    const double tol = d.cg_tol > 0 ? d.cg_tol
+                       : d.cg_stop_rule == UF_STOP_PAPER ? 1e-5
+                       : (d.precision == UF_F64 ? 1e-12 : 1e-7);
+    s0.rule = d.cg_stop_rule;
+    s0.tol2 = d.cg_stop_rule == UF_STOP_PAPER ? tol : tol * tol;
     s0.max_iter = d.cg_max_iter;
     UF_CUDA(cudaMemcpyAsync(st, &s0, sizeof(s0), cudaMemcpyHostToDevice, stream));
     // porosity 1 everywhere (open air): drag coefficient 0 (already zeroed)
@@ -580,19 +588,29 @@ class GridImpl final : public uf_grid {
     else rec_vcycle_sm<uf::SM_JACOBI>(s, mode, cond, use_cond);
   }
 
-  // Non-multigrid preconditioners (one kernel, which also forms r.z).
-  void rec_precond(cudaStream_t s, int mode) {
-    const int kind = d.precond == UF_PRECOND_NONE ? 0 : (d.precond == UF_PRECOND_JACOBI ? 1 : 2);
+  // Non-multigrid preconditioners: one kernel that also forms r.z (and,
+  // under the stop rule of App. A.3, the convergence test); AI2 first forms
+  // y = K r in the level's scratch vector.
+  void rec_precond(cudaStream_t s, int mode, cudaGraphConditionalHandle cond, int use_cond) {
+    const int kind = d.precond == UF_PRECOND_NONE ? 0
+                     : d.precond == UF_PRECOND_JACOBI ? 1
+                     : d.precond == UF_PRECOND_AI1 ? 2 : 3;
     int zc;
     dim3 g = chunk_grid(lv[0].nx, lv[0].ny, lv[0].nz, &zc);
-    L(s, kind == 2 ? "precond_ai1" : (kind == 1 ? "precond_jacobi" : "precond_copy"), 2 * N() * tb(), [&] {
-      uf::k_precond_simple<T><<<g, dim3(uf::BX, uf::BY), 0, s>>>(lv[0], kind, (T)d.ai_omega, z, zc, mode, partials, st);
+    if (kind == 3)
+      L(s, "precond_ai2_K", 2 * N() * tb(), [&] {
+        uf::k_ai2_K<T><<<g, dim3(uf::BX, uf::BY), 0, s>>>(lv[0], (T)d.ai_omega, lv[0].t, zc, st);
+      });
+    const char* names[4] = {"precond_copy", "precond_jacobi", "precond_ai1", "precond_ai2"};
+    L(s, names[kind], 2 * N() * tb(), [&] {
+      uf::k_precond_simple<T><<<g, dim3(uf::BX, uf::BY), 0, s>>>(lv[0], kind, (T)d.ai_omega, z, zc, mode, partials, st,
+                                                                  cond, use_cond);
     });
   }
 
-  void rec_setup_precond(cudaStream_t s) {
+  void rec_setup_precond(cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
     if (d.precond == UF_PRECOND_MG) rec_vcycle(s, 0, 0, 0);
-    else rec_precond(s, 0);
+    else rec_precond(s, 0, cond, use_cond);
   }
 
   void rec_cg_init(cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
@@ -627,7 +645,7 @@ class GridImpl final : public uf_grid {
   uf_status rec_solve(cudaStream_t s, cudaGraphConditionalHandle cond, int* setup_count, int* iter_count) {
     const int before = rec_count;
     rec_cg_init(s, cond, 1);
-    rec_setup_precond(s);
+    rec_setup_precond(s, cond, 1);
     *setup_count = rec_count - before;
     cudaStreamCaptureStatus cs;
     cudaGraph_t cgraph;
@@ -648,7 +666,7 @@ class GridImpl final : public uf_grid {
     UF_CUDA(cudaStreamBeginCaptureToGraph(cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     const int b2 = rec_count;
     rec_cg_iter(cap2, cond, 1);
-    if (d.precond != UF_PRECOND_MG) rec_precond(cap2, 1);
+    if (d.precond != UF_PRECOND_MG) rec_precond(cap2, 1, cond, 1);
     *iter_count = rec_count - b2;
     UF_CUDA(cudaStreamEndCapture(cap2, &body));
     return UF_OK;
@@ -662,13 +680,13 @@ class GridImpl final : public uf_grid {
     UF_CUDA(cudaMemcpyAsync(&conv, &st->converged, sizeof(int), cudaMemcpyDeviceToHost, s));
     UF_CUDA(cudaStreamSynchronize(s));
     if (conv) return UF_OK;
-    rec_setup_precond(s);
+    rec_setup_precond(s, 0, 0);
     for (int it = 0; it < d.cg_max_iter + 1; ++it) {
       rec_cg_iter(s, 0, 0);
       UF_CUDA(cudaMemcpyAsync(&conv, &st->converged, sizeof(int), cudaMemcpyDeviceToHost, s));
       UF_CUDA(cudaStreamSynchronize(s));
       if (conv) break;
-      if (d.precond != UF_PRECOND_MG) rec_precond(s, 1);
+      if (d.precond != UF_PRECOND_MG) rec_precond(s, 1, 0, 0);
     }
     return UF_OK;
   }
@@ -1659,6 +1677,7 @@ void uf_default_desc(uf_grid_desc* d) {
   d->precond = UF_PRECOND_MG; d->cg_tol = 0.0; d->cg_max_iter = 200;
   d->ai_omega = 1.65; d->mg_jacobi_omega = 6.0 / 7.0; d->mg_coarse_max = 512;
   d->mg_smoother = UF_SMOOTH_CHEBY;
+  d->cg_stop_rule = UF_STOP_RESIDUAL;
 }
 
 size_t uf_workspace_bytes(const uf_grid_desc* d) {

@@ -133,7 +133,7 @@ __device__ __forceinline__ void cg_init_body(const Level<T>& L, const T* __restr
     if (thread_linear_id() == 0) {
       st->rr = tot[0];
       st->rr0 = tot[0];
-      if (zero_rhs || tot[0] <= st->tol2 * st->bb) {
+      if (zero_rhs || (st->rule == 0 && tot[0] <= st->tol2 * st->bb)) {
         st->converged = 1;
         signal_converged(cond, use_cond, left);
       }
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(NT) k_cg_update(Level<T> L, T* __restrict__ x,
         st->status = DEV_NAN;
         if (st->sticky == 0) st->sticky = DEV_NAN;
         st->converged = 1;
-      } else if (rr <= st->tol2 * st->bb) {
+      } else if (st->rule == 0 && rr <= st->tol2 * st->bb) {
         st->converged = 1;
       } else if (it + 1 >= st->max_iter) {
         st->status = DEV_NOT_CONVERGED;
@@ -287,9 +287,68 @@ __device__ __forceinline__ T ai1_apply(const Level<T>& L, const T* __restrict__ 
   return s * rsqrt(Dc) * ai1_K(L, r, w, i, j, k) + s / Dc * up;
 }
 
+// Second-order approximate inverse (Sec. 3): K = sqrt(2-w) Dbar^-1/2
+// (I + N + N^2) with N = -L Dbar^-1 (strictly lower, entries w_a / Dbar of
+// the lower neighbour), M^-1 = K^T K applied without truncation, as for the
+// first order.  Two passes: y = K r into a scratch vector (k_ai2_K), then
+// z = K^T y (k_precond_simple, kind 3).
+//   (K r)_c   = s Dbar_c^-1/2 (r_c + g_c + sum_{lower m} w g_m / Dbar_m),
+//               g = N r: g_c = sum_{lower n} w r_n / Dbar_n;
+//   (K^T y)_c = s (v_c + h_c + sum_{upper m} w h_m / Dbar_c),
+//               v = Dbar^-1/2 y, h = N^T v: h_c = sum_{upper m} w v_m / Dbar_c.
+template <typename T>
+__device__ __forceinline__ T ai_lower_sum(const Level<T>& L, const T* __restrict__ r, T w, int i, int j, int k) {
+  T g = 0;
+  if (i > 0) g += L.wx * r[lidx(L, i - 1, j, k)] * w / level_diag(L, i - 1, j, k);
+  if (j > 0) g += L.wy * r[lidx(L, i, j - 1, k)] * w / level_diag(L, i, j - 1, k);
+  if (k > 0) g += L.wz * r[lidx(L, i, j, k - 1)] * w / level_diag(L, i, j, k - 1);
+  return g;
+}
+template <typename T>
+__device__ __forceinline__ T ai_upper_v(const Level<T>& L, const T* __restrict__ y, T w, int i, int j, int k) {
+  // sum_{upper m} w_a v_m, v_m = y_m sqrt(w / D_m)
+  T h = 0;
+  if (i < L.nx - 1) h += L.wx * y[lidx(L, i + 1, j, k)] * sqrt(w / level_diag(L, i + 1, j, k));
+  if (j < L.ny - 1) h += L.wy * y[lidx(L, i, j + 1, k)] * sqrt(w / level_diag(L, i, j + 1, k));
+  if (k < L.nz - 1) h += L.wz * y[lidx(L, i, j, k + 1)] * sqrt(w / level_diag(L, i, j, k + 1));
+  return h;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_ai2_K(Level<T> L, T w, T* __restrict__ y, int zc, const SolveState* st) {
+  if (st->converged) return;
+  UF_CELL_LOOP(L);
+  if (!inside) return;
+  for (int k = z0; k < z1; ++k) {
+    T acc = L.r[lidx(L, i, j, k)] + ai_lower_sum(L, L.r, w, i, j, k);
+    if (i > 0) acc += L.wx * ai_lower_sum(L, L.r, w, i - 1, j, k) * w / level_diag(L, i - 1, j, k);
+    if (j > 0) acc += L.wy * ai_lower_sum(L, L.r, w, i, j - 1, k) * w / level_diag(L, i, j - 1, k);
+    if (k > 0) acc += L.wz * ai_lower_sum(L, L.r, w, i, j, k - 1) * w / level_diag(L, i, j, k - 1);
+    y[lidx(L, i, j, k)] = sqrt((T(2) - w) * w / level_diag(L, i, j, k)) * acc;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T ai2_KT(const Level<T>& L, const T* __restrict__ y, T w, int i, int j, int k) {
+  const T s = sqrt(T(2) - w);
+  const T wD = w / level_diag(L, i, j, k);   // 1 / Dbar_c
+  T hh = 0;                                  // sum_{upper m} w_a h_m
+  if (i < L.nx - 1) hh += L.wx * (w / level_diag(L, i + 1, j, k)) * ai_upper_v(L, y, w, i + 1, j, k);
+  if (j < L.ny - 1) hh += L.wy * (w / level_diag(L, i, j + 1, k)) * ai_upper_v(L, y, w, i, j + 1, k);
+  if (k < L.nz - 1) hh += L.wz * (w / level_diag(L, i, j, k + 1)) * ai_upper_v(L, y, w, i, j, k + 1);
+  const T v = y[lidx(L, i, j, k)] * sqrt(wD);
+  const T h = wD * ai_upper_v(L, y, w, i, j, k);
+  return s * (v + h + wD * hh);
+}
+
+// z = M^-1 r for the simple preconditioners and rz = r.z (kind 0: copy,
+// 1: Jacobi, 2: AI1, 3: AI2 from y = K r in L.t).  Under the stop rule of
+// App. A.3 (st->rule 1) the convergence test r.z <= tol ||b||^2 happens
+// here, where r.z is formed.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_precond_simple(Level<T> L, int kind, T w, T* __restrict__ z, int zc, int mode,
-                                                       double* partials, SolveState* st) {
+                                                       double* partials, SolveState* st,
+                                                       cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ double sh[32];
   __shared__ bool last;
   if (st->converged) return;
@@ -305,8 +364,10 @@ __global__ void __launch_bounds__(NT) k_precond_simple(Level<T> L, int kind, T w
         zv = rv;
       } else if (kind == 1) {
         zv = rv / level_diag(L, i, j, k);
-      } else {
+      } else if (kind == 2) {
         zv = ai1_apply(L, L.r, w, i, j, k);
+      } else {
+        zv = ai2_KT(L, L.t, w, i, j, k);
       }
       z[c] = zv;
       dacc.add(L.r[c], zv);
@@ -320,6 +381,10 @@ __global__ void __launch_bounds__(NT) k_precond_simple(Level<T> L, int kind, T w
     reduce_partials_sum<NT, 1>(partials, tot, sh);
     if (thread_linear_id() == 0) {
       finish_rz(st, tot[0], mode);
+      if (st->rule == 1 && tot[0] <= st->tol2 * st->bb) {
+        st->converged = 1;
+        if (use_cond) cudaGraphSetConditional(cond, 0);
+      }
       st->ticket[0] = 0u;
     }
   }

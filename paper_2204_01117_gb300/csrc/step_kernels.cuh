@@ -407,8 +407,10 @@ __device__ __forceinline__ T cell_flux(const StepParams<T>& p, const T* __restri
 
 // Solver scalars shared by the pressure-solve kernels (device memory).
 struct SolveState {
-  double bb, rr, rz, dq, alpha, beta, rr0, tol2;
+  double bb, rr, rz, dq, alpha, beta, rr0;
+  double tol2;   // stop rule 0: tol^2 (rr <= tol2 bb); rule 1: tol (rz <= tol2 bb)
   int iter, converged, status, max_iter, sticky;
+  int rule;      // 0: ||r|| <= tol ||b||;  1: r.z <= tol ||b||^2 (App. A.3)
   unsigned int ticket[4];
   long long total_iters;   // CG iterations since the grid was created
 };

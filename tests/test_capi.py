@@ -111,3 +111,10 @@ def test_batch_null_arguments_are_errors(lib):
     assert lib.uf_get_tuning(None, None, None) == uf.UF_ERR_ARG
     assert lib.uf_set_tuning(None, None) == uf.UF_ERR_ARG
     assert lib.uf_autotune(None, 1, None, None) == uf.UF_ERR_ARG
+
+
+def test_paper_stop_rule_needs_a_simple_preconditioner(lib):
+    assert uf.workspace_bytes(uf.default_desc(precond="mg", cg_stop_rule="paper")) == 0
+    assert "App. A.3" in uf.last_error()
+    assert uf.workspace_bytes(uf.default_desc(precond="ai2", cg_stop_rule="paper")) > 0
+    assert uf.workspace_bytes(uf.default_desc(cg_stop_rule=2)) == 0

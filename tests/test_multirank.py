@@ -33,7 +33,7 @@ def _rank_main(rank, world, port, out):
 
 def test_weak_scaling_rate_over_two_gloo_ranks():
     world = 2
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_rank_main, args=(world, _free_port(), out), nprocs=world, join=True)
     for r in range(world):
         rate, slowest, env = out[r]
@@ -60,6 +60,6 @@ def _reference_rank(rank, world, port, out):
 
 
 def test_reference_arm_runs_on_rank_zero_only():
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_reference_rank, args=(2, _free_port(), out), nprocs=2, join=True)
     assert out[1] == 0
