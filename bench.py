@@ -12,7 +12,9 @@ needed between steps.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 The line also carries "adjoint": the adjoint/forward time ratio on the
-128 x 128 x 48 parametric design workload (see adjoint_leg), and "batched":
+128 x 128 x 48 parametric design workload (see adjoint_leg), with one
+iteration of the gradient-descent design loop and its wind-direction
+robustness re-runs (see design_loop_leg), and "batched":
 32 instances of uneven size and wind direction advanced by the batched
 persistent launches, against the same instances stepped one after another
 (see batched_leg).
@@ -218,16 +220,93 @@ def adjoint_leg():
     tf, Jf = forward()
     ta, Ja = adjoint()
     grad = g.design_vjp(d.boxes, d.theta, d.width, dphi)
+    design = design_loop_leg(g, d, x0, dphi, tf)
     out = {"workload": f"design lattice {d.nx}x{d.ny}x{d.nz}, h={d.h} m, 12 parametric buildings "
                        f"(36 parameters), {d.steps} steps at fixed dt={d.fixed_dt} s, checkpoints every "
                        f"{d.ckpt_every}, FP32 fields + FP64 reductions",
            "forward_ms": tf * 1e3, "adjoint_ms": ta * 1e3, "ratio": ta / tf,
            "J": Jf, "J_matches_forward": bool(Ja == Jf),
            "grad_norm": float(sum(x * x for x in grad)) ** 0.5,
-           "workspace_bytes": int(g.lib.uf_adjoint_workspace_bytes(g._h, d.steps, d.ckpt_every))}
+           "workspace_bytes": int(g.lib.uf_adjoint_workspace_bytes(g._h, d.steps, d.ckpt_every)),
+           "design_loop": design}
     g.free_adjoint_workspace()
     g.close()
     return out
+
+
+def design_loop_leg(g, d, x0, dphi, forward_s):
+    """One iteration of the gradient-descent design loop of Sec. 6 on the
+    same workload, with the region-average objective L = sum_i (ubar_i -
+    u_t)^2 over the six pedestrian-level target regions (u_t = 0.55 m/s):
+    design map + uf_adjoint_run_ex + design VJP, wall clock, device
+    synchronised on both sides, after one untimed iteration.  The paper's
+    forward-difference gradient needs (parameters + 1) forward runs per
+    iteration; that cost is given as the measured forward time times 37.
+    Then the +-10 degree robustness re-runs: the three wind directions of
+    the design advanced by one batch against three single grids in turn,
+    each timed over the 200 steps with CUDA events."""
+    import numpy as np
+    import torch
+    from paper_2204_01117_gb300 import uf
+    obj = {"kind": "regions", "regions": d.regions, "u_t": d.u_t}
+
+    def iteration():
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        g.design_to_phi(d.boxes, d.theta, d.width)
+        g.set_fields(x0)
+        L, _ = g.adjoint_run(d.steps, d.ckpt_every, out=dphi, objective=obj)
+        grad = g.design_vjp(d.boxes, d.theta, d.width, dphi)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, L, grad
+
+    iteration()
+    ti, L, grad = iteration()
+    nparam = d.theta.size
+    phi = g.design_to_phi(d.boxes, d.theta, d.width, set_porosity=False)
+    winds = (-10.0, 0.0, 10.0)
+    params = [dict(d.params(), nx=d.nx, ny=d.ny, nz=d.nz, wind_dir_deg=w) for w in winds]
+    b = uf.Batch(params, precision="f32")
+    for gb in b.grids:
+        gb.set_porosity(phi)
+        gb.init_state()
+    b.run(3, stats=False)
+    for gb in b.grids:
+        gb.init_state()
+
+    def timed(run, stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    t_batch = timed(lambda: b.run(d.steps, stats=False), b.stream)
+    L_batch = [gb.objective_ex(obj) for gb in b.grids]
+    b.close()
+    solos = []
+    for p in params:
+        q = dict(p)
+        nx, ny, nz = q.pop("nx"), q.pop("ny"), q.pop("nz")
+        s = uf.Grid(nx, ny, nz, precision="f32", stream=g.stream, **q)
+        s.set_porosity(phi)
+        s.init_state()
+        s.run(3, stats=False)
+        s.init_state()
+        solos.append(s)
+    t_seq = timed(lambda: [s.run(d.steps, stats=False) for s in solos], g.stream)
+    L_seq = [s.objective_ex(obj) for s in solos]
+    for s in solos:
+        s.close()
+    return {"objective": "region average, 6 pedestrian-level regions z in [0, 3] m, u_t = 0.55 m/s",
+            "parameters": nparam, "L": L, "grad_norm": float(np.linalg.norm(grad)),
+            "iteration_ms": ti * 1e3,
+            "forward_difference_iteration_ms": (nparam + 1) * forward_s * 1e3,
+            "speedup_vs_forward_differences": (nparam + 1) * forward_s / ti,
+            "robustness": {"winds_deg": list(winds), "L": L_batch, "batched_ms": t_batch,
+                           "sequential_ms": t_seq, "batch_equals_solo": L_batch == L_seq}}
 
 
 # ---------------------------------------------------------------- batched leg

@@ -227,6 +227,31 @@ int uf_last_step_launches(uf_grid* g);
  * Builds the step graphs if needed. */
 uf_status uf_launch_counts(uf_grid* g, int* fixed, int* per_iter);
 
+/* ---- Objectives ----------------------------------------------------------
+ * UF_OBJ_COMFORT: the pedestrian comfort band of uf_objective, sum over the
+ *   cells with centre height in [z_lo, z_hi] of max(|u_c| - u_hi, 0)^2 +
+ *   max(u_lo - |u_c|, 0)^2.
+ * UF_OBJ_REGIONS: the region-average objective of Sec. 6 ("Avoiding Heat
+ *   Pockets in Early Design Stages"), L = sum_i (ubar_i - u_t)^2, ubar_i the
+ *   mean of |u_c| over the cells whose centres lie in box i (regions[6i ..
+ *   6i+5] = x0, x1, y0, y1, z0, z1 in m, host array); every box must hold at
+ *   least one cell centre.
+ * |u_c|: speed from the face averages at the cell centre. */
+#define UF_MAX_REGIONS 8
+enum { UF_OBJ_COMFORT = 0, UF_OBJ_REGIONS = 1 };
+typedef struct {
+  int kind;                  /* UF_OBJ_*                                      */
+  double z_lo, z_hi, u_hi, u_lo;   /* comfort band                            */
+  int nreg;                  /* regions: 1..UF_MAX_REGIONS                    */
+  const double* regions;     /* 6 * nreg values                               */
+  double u_t;                /* target speed [m/s] (0.55 in Sec. 6)           */
+} uf_objective_desc;
+
+/* The objective of the current state (synchronises).  Errors: UF_ERR_ARG
+ * for a NULL descriptor or output, an unknown kind, nreg outside
+ * 1..UF_MAX_REGIONS, a NULL region array or a box with no cell centre. */
+uf_status uf_objective_ex(uf_grid* g, const uf_objective_desc* obj, double* J_out);
+
 /* ---- Discrete adjoint and design gradients ----------------------------
  * The paper obtains design gradients by forward differences, N+1 forward
  * simulations per gradient (Sec. 4, "Automatic Design Optimization";
@@ -255,6 +280,11 @@ size_t uf_adjoint_workspace_bytes(uf_grid* g, int nsteps, int ckpt_every);
  * UF_ERR_STATE, and the solver errors of uf_step. */
 uf_status uf_adjoint_run(uf_grid* g, void* d_ws, size_t bytes, int nsteps, int ckpt_every, double z_lo, double z_hi,
                          double u_hi, double u_lo, void* dJ_dphi, double* J_out);
+
+/* uf_adjoint_run for any objective of uf_objective_ex; the descriptor is
+ * checked, with the errors of uf_objective_ex, before any step runs. */
+uf_status uf_adjoint_run_ex(uf_grid* g, void* d_ws, size_t bytes, int nsteps, int ckpt_every,
+                            const uf_objective_desc* obj, void* dJ_dphi, double* J_out);
 
 /* Vector-Jacobian product of one step (uf_step with the grid's fixed dt) at
  * the grid's current state X: given lam_out, the cotangent of the step's

@@ -272,6 +272,34 @@ class Oracle:
         return st
 
 
+def cell_speed(u, v, w) -> np.ndarray:
+    """|u_c| at every cell centre from the face averages of the three
+    staggered components (arrays shaped (nz, ny, nx+1), (nz, ny+1, nx),
+    (nz+1, ny, nx))."""
+    uc = 0.5 * (u[:, :, :-1] + u[:, :, 1:])
+    vc = 0.5 * (v[:, :-1, :] + v[:, 1:, :])
+    wc = 0.5 * (w[:-1, :, :] + w[1:, :, :])
+    return np.sqrt(uc * uc + vc * vc + wc * wc)
+
+
+def region_objective(u, v, w, h: float, regions, u_t: float):
+    """Region-average objective of Sec. 6 ("Avoiding Heat Pockets in Early
+    Design Stages"): L = sum_i (ubar_i - u_t)^2 with ubar_i the mean cell
+    speed over the cells whose centres lie in box i = (x0, x1, y0, y1, z0,
+    z1) [m].  Returns (L, [ubar_i])."""
+    speed = cell_speed(u, v, w)
+    nz, ny, nx = speed.shape
+    z, y, x = np.meshgrid((np.arange(nz) + 0.5) * h, (np.arange(ny) + 0.5) * h, (np.arange(nx) + 0.5) * h,
+                          indexing="ij")
+    means = []
+    for x0, x1, y0, y1, z0, z1 in np.asarray(regions, dtype=np.float64).reshape(-1, 6):
+        sel = (x >= x0) & (x <= x1) & (y >= y0) & (y <= y1) & (z >= z0) & (z <= z1)
+        if not sel.any():
+            raise ValueError("region holds no cell centre")
+        means.append(float(speed[sel].mean()))
+    return float(sum((m - u_t) ** 2 for m in means)), means
+
+
 def design_to_phi(nx: int, ny: int, nz: int, h: float, boxes, theta, width: float) -> np.ndarray:
     """Porosity of the parametric design, in FP64 numpy: the product over
     boxes of (1 - chi), chi the product of five logistic ramps at the cell

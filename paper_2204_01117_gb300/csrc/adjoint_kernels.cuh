@@ -674,6 +674,29 @@ __global__ void __launch_bounds__(NT) k_objective_adj(StepParams<T> p, const T* 
   aadd(&lw[idx_c(p, i, j, k + 1)], gz);
 }
 
+// Seed of the region-average objective for one region: dL/du_c = coef u_c /
+// |u_c| on the cells of the box, coef = 2 (mean speed - u_t) / cell count,
+// scattered half to each of the two faces of every component.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_box_speed_adj(StepParams<T> p, const T* __restrict__ u,
+                                                      const T* __restrict__ v, const T* __restrict__ w, int i0, int i1,
+                                                      int j0, int j1, int k0, double coef, T* lu, T* lv, T* lw) {
+  const int i = i0 + blockIdx.x * BX + threadIdx.x, j = j0 + blockIdx.y * BY + threadIdx.y, k = k0 + blockIdx.z;
+  if (i > i1 || j > j1) return;
+  const double uc = 0.5 * ((double)u[idx_u(p, i, j, k)] + (double)u[idx_u(p, i + 1, j, k)]);
+  const double vc = 0.5 * ((double)v[idx_v(p, i, j, k)] + (double)v[idx_v(p, i, j + 1, k)]);
+  const double wc = 0.5 * ((double)w[idx_c(p, i, j, k)] + (double)w[idx_c(p, i, j, k + 1)]);
+  const double s = sqrt(uc * uc + vc * vc + wc * wc);
+  if (!(s > 0.0)) return;
+  const T gx = (T)(0.5 * coef * uc / s), gy = (T)(0.5 * coef * vc / s), gz = (T)(0.5 * coef * wc / s);
+  aadd(&lu[idx_u(p, i, j, k)], gx);
+  aadd(&lu[idx_u(p, i + 1, j, k)], gx);
+  aadd(&lv[idx_v(p, i, j, k)], gy);
+  aadd(&lv[idx_v(p, i, j + 1, k)], gy);
+  aadd(&lw[idx_c(p, i, j, k)], gz);
+  aadd(&lw[idx_c(p, i, j, k + 1)], gz);
+}
+
 // dJ/dphi = dJ/dc * dc/dphi with c = C_d a ((1-phi)/(phi+e))^b, in FP64.
 template <typename T>
 __global__ void k_dphi(const T* __restrict__ phi, const T* __restrict__ lc, T* __restrict__ out, size_t n, double Cd,

@@ -964,6 +964,17 @@ class GridImpl final : public uf_grid {
 
   uf_status adjoint_run(void* wsp, size_t bytes, int nsteps, int C, double z_lo, double z_hi, double u_hi, double u_lo,
                         void* dJ_dphi, double* J_out) override {
+    uf_objective_desc od;
+    std::memset(&od, 0, sizeof(od));
+    od.kind = UF_OBJ_COMFORT;
+    od.z_lo = z_lo; od.z_hi = z_hi; od.u_hi = u_hi; od.u_lo = u_lo;
+    return adjoint_run_ex(wsp, bytes, nsteps, C, &od, dJ_dphi, J_out);
+  }
+
+  uf_status adjoint_run_ex(void* wsp, size_t bytes, int nsteps, int C, const uf_objective_desc* od, void* dJ_dphi,
+                           double* J_out) override {
+    uf_status s0 = check_objective(od);
+    if (s0 != UF_OK) return s0;
     if (!(d.fixed_dt > 0)) return fail(UF_ERR_ARG, "uf_adjoint_run needs a fixed time step (fixed_dt > 0)");
     if (!have_state) return fail(UF_ERR_STATE, "no state: call uf_init_state or uf_set_state first");
     if (!wsp || nsteps < 1 || C < 1) return fail(UF_ERR_ARG, "need a workspace, nsteps >= 1 and ckpt_every >= 1");
@@ -993,20 +1004,13 @@ class GridImpl final : public uf_grid {
     s = check_device(nullptr);
     if (s != UF_OK) return s;
     double J = 0.0;
-    s = objective(z_lo, z_hi, u_hi, u_lo, &J);
+    std::vector<double> means;
+    s = objective_ex_means(od, &J, &means);
     if (s != UF_OK) return s;
     if (J_out) *J_out = J;
     // 2. seed: dJ/du of the final state
-    int k_lo = d.nz, k_hi = -1;
-    for (int k = 0; k < d.nz; ++k) {
-      const double zc = (k + 0.5) * d.h;
-      if (zc >= z_lo && zc <= z_hi) { k_lo = std::min(k_lo, k); k_hi = std::max(k_hi, k); }
-    }
-    const dim3 blk(uf::BX, uf::BY);
-    if (k_hi >= k_lo)
-      uf::k_objective_adj<T><<<plane_grid(d.nx, d.ny, k_hi - k_lo + 1), blk, 0, stream>>>(sp, u, v, w, k_lo, k_hi, u_hi,
-                                                                                          u_lo, R.L1.u, R.L1.v, R.L1.w);
-    UF_CUDA(cudaGetLastError());
+    s = seed_objective(od, means, R.L1);
+    if (s != UF_OK) return s;
     // 3. reverse sweep, one checkpoint segment at a time
     for (int seg = A.nseg - 1; seg >= 0; --seg) {
       const int n0 = seg * C, n1 = std::min(nsteps, n0 + C);
@@ -1578,6 +1582,93 @@ class GridImpl final : public uf_grid {
     return UF_OK;
   }
 
+  // ------------------------------------------------------------- objectives
+  // Cell index range whose centres lie in [a, b] (m) along an axis of n cells.
+  void centre_range(double a, double b, int n, int* lo, int* hi) const {
+    *lo = std::max(0, (int)std::ceil(a / d.h - 0.5));
+    *hi = std::min(n - 1, (int)std::floor(b / d.h - 0.5));
+  }
+  struct Box {
+    int i0, i1, j0, j1, k0, k1;
+    long long cells() const { return (long long)(i1 - i0 + 1) * (j1 - j0 + 1) * (k1 - k0 + 1); }
+  };
+  Box region_box(const double* r6) const {
+    Box B;
+    centre_range(r6[0], r6[1], d.nx, &B.i0, &B.i1);
+    centre_range(r6[2], r6[3], d.ny, &B.j0, &B.j1);
+    centre_range(r6[4], r6[5], d.nz, &B.k0, &B.k1);
+    return B;
+  }
+  uf_status check_objective(const uf_objective_desc* od) const {
+    if (!od) return fail(UF_ERR_ARG, "NULL objective");
+    if (od->kind == UF_OBJ_COMFORT) return UF_OK;
+    if (od->kind != UF_OBJ_REGIONS) return fail(UF_ERR_ARG, "unknown objective kind");
+    if (od->nreg < 1 || od->nreg > UF_MAX_REGIONS || !od->regions)
+      return fail(UF_ERR_ARG, "regions objective needs 1..8 regions");
+    for (int r = 0; r < od->nreg; ++r) {
+      const Box B = region_box(od->regions + 6 * r);
+      if (B.i1 < B.i0 || B.j1 < B.j0 || B.k1 < B.k0)
+        return fail(UF_ERR_ARG, "region " + std::to_string(r) + " holds no cell centre");
+    }
+    return UF_OK;
+  }
+
+  // The objective; for regions also the mean speed of each region.
+  uf_status objective_ex_means(const uf_objective_desc* od, double* J, std::vector<double>* means) {
+    uf_status s = check_objective(od);
+    if (s != UF_OK) return s;
+    if (od->kind == UF_OBJ_COMFORT) return objective(od->z_lo, od->z_hi, od->u_hi, od->u_lo, J);
+    const dim3 blk(uf::BX, uf::BY);
+    for (int r = 0; r < od->nreg; ++r) {
+      const Box B = region_box(od->regions + 6 * r);
+      int zc;
+      dim3 g = chunk_grid(B.i1 - B.i0 + 1, B.j1 - B.j0 + 1, B.k1 - B.k0 + 1, &zc);
+      uf::k_box_speed<T><<<g, blk, 0, stream>>>(sp, u, v, w, B.i0, B.i1, B.j0, B.j1, B.k0, B.k1, zc, partials,
+                                                 &st->ticket[0], scal + r);
+    }
+    UF_CUDA(cudaGetLastError());
+    double sums[UF_MAX_REGIONS];
+    UF_CUDA(cudaMemcpyAsync(sums, scal, sizeof(double) * od->nreg, cudaMemcpyDeviceToHost, stream));
+    UF_CUDA(cudaStreamSynchronize(stream));
+    double L = 0.0;
+    if (means) means->assign(od->nreg, 0.0);
+    for (int r = 0; r < od->nreg; ++r) {
+      const double m = sums[r] / (double)region_box(od->regions + 6 * r).cells();
+      if (means) (*means)[r] = m;
+      L += (m - od->u_t) * (m - od->u_t);
+    }
+    *J = L;
+    return UF_OK;
+  }
+  uf_status objective_ex(const uf_objective_desc* od, double* J) override {
+    if (!J) return fail(UF_ERR_ARG, "NULL output");
+    return objective_ex_means(od, J, nullptr);
+  }
+
+  // dJ/du of the current state into the face adjoints L (accumulated).
+  uf_status seed_objective(const uf_objective_desc* od, const std::vector<double>& means, const FaceSet& Lf) {
+    const dim3 blk(uf::BX, uf::BY);
+    if (od->kind == UF_OBJ_COMFORT) {
+      int k_lo = d.nz, k_hi = -1;
+      for (int k = 0; k < d.nz; ++k) {
+        const double zc = (k + 0.5) * d.h;
+        if (zc >= od->z_lo && zc <= od->z_hi) { k_lo = std::min(k_lo, k); k_hi = std::max(k_hi, k); }
+      }
+      if (k_hi >= k_lo)
+        uf::k_objective_adj<T><<<plane_grid(d.nx, d.ny, k_hi - k_lo + 1), blk, 0, stream>>>(
+            sp, u, v, w, k_lo, k_hi, od->u_hi, od->u_lo, Lf.u, Lf.v, Lf.w);
+    } else {
+      for (int r = 0; r < od->nreg; ++r) {
+        const Box B = region_box(od->regions + 6 * r);
+        const double coef = 2.0 * (means[r] - od->u_t) / (double)B.cells();
+        uf::k_box_speed_adj<T><<<plane_grid(B.i1 - B.i0 + 1, B.j1 - B.j0 + 1, B.k1 - B.k0 + 1), blk, 0, stream>>>(
+            sp, u, v, w, B.i0, B.i1, B.j0, B.j1, B.k0, coef, Lf.u, Lf.v, Lf.w);
+      }
+    }
+    UF_CUDA(cudaGetLastError());
+    return UF_OK;
+  }
+
   uf_status objective(double z_lo, double z_hi, double u_hi, double u_lo, double* J) override {
     if (!J) return fail(UF_ERR_ARG, "NULL output");
     int k_lo = d.nz, k_hi = -1;
@@ -1763,6 +1854,15 @@ uf_status uf_set_fields(uf_grid* g, int n, const int* fields, const void* const*
 uf_status uf_get_fields(uf_grid* g, int n, const int* fields, void* const* bufs) {
   UF_NEED(g);
   return g->get_fields(n, fields, bufs);
+}
+uf_status uf_objective_ex(uf_grid* g, const uf_objective_desc* obj, double* J_out) {
+  UF_NEED(g);
+  return g->objective_ex(obj, J_out);
+}
+uf_status uf_adjoint_run_ex(uf_grid* g, void* d_ws, size_t bytes, int nsteps, int ckpt_every,
+                            const uf_objective_desc* obj, void* dJ_dphi, double* J_out) {
+  UF_NEED(g);
+  return g->adjoint_run_ex(d_ws, bytes, nsteps, ckpt_every, obj, dJ_dphi, J_out);
 }
 uf_status uf_step_vjp(uf_grid* g, void* d_ws, size_t bytes, const void* const* lam_out, void* const* lam_in,
                       void* lam_phi) {

@@ -55,6 +55,8 @@ struct uf_grid {
   virtual uf_status profile_step(uf_kernel_time*, int, int*, uf_step_stats*) = 0;
   virtual size_t adjoint_bytes(int, int) = 0;
   virtual uf_status adjoint_run(void*, size_t, int, int, double, double, double, double, void*, double*) = 0;
+  virtual uf_status objective_ex(const uf_objective_desc*, double*) = 0;
+  virtual uf_status adjoint_run_ex(void*, size_t, int, int, const uf_objective_desc*, void*, double*) = 0;
   virtual uf_status step_vjp(void*, size_t, const void* const*, void* const*, void*) = 0;
   virtual uf_status design_phi(int, const double*, const double*, double, void*) = 0;
   virtual uf_status design_vjp(int, const double*, const double*, double, const void*, double*) = 0;

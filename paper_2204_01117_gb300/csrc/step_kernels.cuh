@@ -600,6 +600,39 @@ __global__ void __launch_bounds__(NT) k_objective(StepParams<T> p, const T* __re
   }
 }
 
+// Sum of the cell-centre speed |u_c| over the cell box [i0, i1] x [j0, j1] x
+// [k0, k1] (one target region of the region-average objective of Sec. 6,
+// "Avoiding Heat Pockets"); deterministic FP64 reduction into *out.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_box_speed(StepParams<T> p, const T* __restrict__ u, const T* __restrict__ v,
+                                                  const T* __restrict__ w, int i0, int i1, int j0, int j1, int k0,
+                                                  int k1, int zc, double* partials, unsigned int* ticket,
+                                                  double* out) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  const int i = i0 + blockIdx.x * BX + threadIdx.x, j = j0 + blockIdx.y * BY + threadIdx.y;
+  const int z0 = k0 + blockIdx.z * zc, z1 = min(k1 + 1, z0 + zc);
+  double acc = 0.0;
+  if (i <= i1 && j <= j1) {
+    for (int k = z0; k < z1; ++k) {
+      const double uc = 0.5 * ((double)u[idx_u(p, i, j, k)] + (double)u[idx_u(p, i + 1, j, k)]);
+      const double vc = 0.5 * ((double)v[idx_v(p, i, j, k)] + (double)v[idx_v(p, i, j + 1, k)]);
+      const double wc = 0.5 * ((double)w[idx_c(p, i, j, k)] + (double)w[idx_c(p, i, j, k + 1)]);
+      acc += sqrt(uc * uc + vc * vc + wc * wc);
+    }
+  }
+  acc = block_sum<NT>(acc, sh);
+  const double vals[1] = {acc};
+  if (publish_partials<1>(partials, ticket, vals, &last)) {
+    double tot[1];
+    reduce_partials_sum<NT, 1>(partials, tot, sh);
+    if (thread_linear_id() == 0) {
+      *out = tot[0];
+      *ticket = 0u;
+    }
+  }
+}
+
 // ---------------------------------------------------- diagnostics --------
 // Partial sums of (h div u)^2 and |u_c|^2 over all cells.
 template <typename T>

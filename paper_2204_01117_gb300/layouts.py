@@ -213,6 +213,8 @@ class DesignScenario(Scenario):
     width: float = 2.0                  # logistic ramp width [m]
     fixed_dt: float = 0.2               # [s]
     ckpt_every: int = 20
+    regions: np.ndarray = None          # (nreg, 6): x0, x1, y0, y1, z0, z1 of each target region [m]
+    u_t: float = 0.55                   # target mean wind speed of a region [m/s]
 
     def params(self) -> dict:
         d = super().params()
@@ -227,7 +229,10 @@ def design_lattice(nx=128, ny=128, nz=48, h=2.0, cols=4, rows=3, footprint=20.0,
     likewise for rows), heights drawn uniformly, shifts zero; log-law
     inflow along +x; one-cell logistic ramps; the fixed time step of 0.2 s
     used for the design runs of Sec. 6 ("Avoiding Heat Pockets in Early
-    Design Stages").  Draw order: one height per building, row by row."""
+    Design Stages").  Draw order: one height per building, row by row.
+    Target regions of the region-average objective (six in Sec. 6): square
+    frames of one footprint side at pedestrian level, z in [0, 3] m, centred
+    between four neighbouring buildings, for the first two row gaps."""
     rng = SplitMix64(seed)
     lx, ly = nx * h, ny * h
     boxes, theta = [], []
@@ -236,11 +241,16 @@ def design_lattice(nx=128, ny=128, nz=48, h=2.0, cols=4, rows=3, footprint=20.0,
             cx, cy = lx * (c + 1) / (cols + 1), ly * (r + 1) / (rows + 1)
             boxes.append((cx - footprint / 2, cx + footprint / 2, cy - footprint / 2, cy + footprint / 2))
             theta.append((rng.uniform(*height), 0.0, 0.0))
+    regions = []
+    for r in range(min(rows - 1, 2)):
+        for c in range(cols - 1):
+            gx, gy = lx * (c + 1.5) / (cols + 1), ly * (r + 1.5) / (rows + 1)
+            regions.append((gx - footprint / 2, gx + footprint / 2, gy - footprint / 2, gy + footprint / 2, 0.0, 3.0))
     return DesignScenario(nx, ny, nz, h, np.ones((nz, ny, nx)), wind_dir_deg=0.0, u_ref=u_ref, z_ref=10.0,
                           z0=0.5, inflow_loglaw=True, ground_noslip=True, steps=steps,
                           name=f"design_{nx}x{ny}x{nz}_{cols * rows}b_s{seed}",
                           boxes=np.array(boxes), theta=np.array(theta), width=h, fixed_dt=fixed_dt,
-                          ckpt_every=ckpt_every)
+                          ckpt_every=ckpt_every, regions=np.array(regions).reshape(-1, 6))
 
 
 def empty_domain(nx, ny, nz, h=1.0, u_ref=2.0, wind_dir_deg=0.0, ground_noslip=False,

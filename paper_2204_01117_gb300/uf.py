@@ -62,6 +62,34 @@ class StepStats(ctypes.Structure):
 
 
 MAX_LEVELS = 16
+MAX_REGIONS = 8
+
+
+class ObjectiveDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("z_lo", ctypes.c_double), ("z_hi", ctypes.c_double),
+                ("u_hi", ctypes.c_double), ("u_lo", ctypes.c_double), ("nreg", ctypes.c_int),
+                ("regions", ctypes.POINTER(ctypes.c_double)), ("u_t", ctypes.c_double)]
+
+
+def objective_desc(objective=None, band=(1.0, 3.0, 4.0, 1.0)):
+    """(uf_objective_desc, keep-alive).  objective: None or {"kind":
+    "comfort", "band": (z_lo, z_hi, u_hi, u_lo)} for the comfort band, or
+    {"kind": "regions", "regions": [(x0, x1, y0, y1, z0, z1), ...], "u_t":
+    0.55} for the region-average objective of Sec. 6."""
+    d = ObjectiveDesc()
+    keep = None
+    if objective is None or objective.get("kind", "comfort") == "comfort":
+        b = band if objective is None else objective.get("band", band)
+        d.kind = 0
+        d.z_lo, d.z_hi, d.u_hi, d.u_lo = b
+    else:
+        r = np.ascontiguousarray(np.asarray(objective["regions"], dtype=np.float64).reshape(-1, 6))
+        d.kind = 1
+        d.nreg = r.shape[0]
+        d.regions = r.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.u_t = float(objective.get("u_t", 0.55))
+        keep = r
+    return d, keep
 
 
 class Tuning(ctypes.Structure):
@@ -164,6 +192,10 @@ def load():
     lib.uf_set_fields.restype = ip
     lib.uf_get_fields.argtypes = [vp, ip, P(ip), P(vp)]
     lib.uf_get_fields.restype = ip
+    lib.uf_objective_ex.argtypes = [vp, P(ObjectiveDesc), P(dp)]
+    lib.uf_objective_ex.restype = ip
+    lib.uf_adjoint_run_ex.argtypes = [vp, vp, ctypes.c_size_t, ip, ip, P(ObjectiveDesc), vp, P(dp)]
+    lib.uf_adjoint_run_ex.restype = ip
     lib.uf_step_vjp.argtypes = [vp, vp, ctypes.c_size_t, P(vp), P(vp), vp]
     lib.uf_step_vjp.restype = ip
     lib.uf_design_to_phi.argtypes = [vp, ip, P(dp), P(dp), dp, vp]
@@ -393,6 +425,13 @@ class Grid:
         check(self.lib.uf_objective(self._h, z_lo, z_hi, u_hi, u_lo, ctypes.byref(J)))
         return J.value
 
+    def objective_ex(self, objective) -> float:
+        """Any objective of uf_objective_ex (see objective_desc)."""
+        d, keep = objective_desc(objective)
+        J = ctypes.c_double()
+        check(self.lib.uf_objective_ex(self._h, ctypes.byref(d), ctypes.byref(J)))
+        return J.value
+
     def divergence(self) -> float:
         out = ctypes.c_double()
         check(self.lib.uf_divergence(self._h, ctypes.byref(out)))
@@ -426,7 +465,8 @@ class Grid:
         return s, out
 
     # -- design gradients ------------------------------------------------
-    def adjoint_run(self, nsteps: int, ckpt_every: int = 20, z_lo=1.0, z_hi=3.0, u_hi=4.0, u_lo=1.0, out=None):
+    def adjoint_run(self, nsteps: int, ckpt_every: int = 20, z_lo=1.0, z_hi=3.0, u_hi=4.0, u_lo=1.0, out=None,
+                    objective=None):
         """Forward nsteps from the current state, objective, reverse sweep.
         Returns (J, dJ/dphi) -- dJ/dphi in ``out`` (a CUDA tensor or numpy
         array of the grid's precision) or a new numpy array; the grid ends at
@@ -444,8 +484,13 @@ class Grid:
             out = np.empty(self.shapes["phi"], dtype=self.np_dtype)
         optr, keep = self._arg(out)
         J = ctypes.c_double()
-        check(self.lib.uf_adjoint_run(self._h, ctypes.c_void_p(ws.data_ptr()), nbytes, nsteps, ckpt_every, z_lo, z_hi,
-                                      u_hi, u_lo, optr, ctypes.byref(J)))
+        if objective is None:
+            check(self.lib.uf_adjoint_run(self._h, ctypes.c_void_p(ws.data_ptr()), nbytes, nsteps, ckpt_every, z_lo,
+                                          z_hi, u_hi, u_lo, optr, ctypes.byref(J)))
+        else:
+            d, dkeep = objective_desc(objective)
+            check(self.lib.uf_adjoint_run_ex(self._h, ctypes.c_void_p(ws.data_ptr()), nbytes, nsteps, ckpt_every,
+                                             ctypes.byref(d), optr, ctypes.byref(J)))
         return J.value, out
 
     STATE5 = ("u", "v", "w", "k", "omega")
@@ -667,14 +712,14 @@ def _make_functions():
         (uf_adjoint_run) and returns dJ/dphi on the device."""
 
         @staticmethod
-        def forward(ctx, phi, grid, x0, nsteps, ckpt_every, band):
+        def forward(ctx, phi, grid, x0, nsteps, ckpt_every, objective):
             phi = phi.detach().contiguous()
             grid.set_porosity(phi)
             grid.set_fields(x0)
             grid.run(nsteps, stats=False)
-            J = grid.objective(*band)
+            J = grid.objective_ex(objective)
             ctx.save_for_backward(phi)
-            ctx.grid, ctx.x0, ctx.nsteps, ctx.ckpt_every, ctx.band = grid, x0, nsteps, ckpt_every, band
+            ctx.grid, ctx.x0, ctx.nsteps, ctx.ckpt_every, ctx.objective = grid, x0, nsteps, ckpt_every, objective
             return torch.tensor(J, dtype=torch.float64, device=phi.device)
 
         @staticmethod
@@ -684,7 +729,7 @@ def _make_functions():
             g.set_porosity(phi)
             g.set_fields(ctx.x0)
             dphi = torch.empty_like(phi)
-            g.adjoint_run(ctx.nsteps, ctx.ckpt_every, *ctx.band, out=dphi)
+            g.adjoint_run(ctx.nsteps, ctx.ckpt_every, out=dphi, objective=ctx.objective)
             return gJ.to(dphi.dtype) * dphi, None, None, None, None, None
 
     class DesignPorosity(torch.autograd.Function):
@@ -719,10 +764,60 @@ def _fns():
     return _functions
 
 
-def comfort_objective(phi, grid: "Grid", x0: dict, nsteps: int, ckpt_every: int = 20, band=(1.0, 3.0, 4.0, 1.0)):
+def comfort_objective(phi, grid: "Grid", x0: dict, nsteps: int, ckpt_every: int = 20, band=(1.0, 3.0, 4.0, 1.0),
+                      objective=None):
     """Differentiable J(phi) (torch.autograd): see ComfortObjective.  phi is a
-    CUDA tensor of the grid's precision and shape (nz, ny, nx)."""
-    return _fns()[0].apply(phi, grid, x0, nsteps, ckpt_every, band)
+    CUDA tensor of the grid's precision and shape (nz, ny, nx); the objective
+    is the comfort band `band` unless `objective` names another one (see
+    objective_desc)."""
+    if objective is None:
+        objective = {"kind": "comfort", "band": tuple(band)}
+    return _fns()[0].apply(phi, grid, x0, nsteps, ckpt_every, objective)
+
+
+def optimize_design(grid: "Grid", boxes, theta0, x0: dict, nsteps: int, iterations: int, step_size: float,
+                    width: float, objective=None, ckpt_every: int = 20, lower=None, upper=None):
+    """Gradient descent on the design parameters (Sec. 4, "Automatic Design
+    Optimization"): theta <- clip(theta - step_size dL/dtheta, lower, upper),
+    the gradient from the discrete adjoint through design_porosity and
+    comfort_objective instead of the N + 1 forward simulations of the paper's
+    forward differences.  The descent sign is the reading of the paper's
+    update rule.  Returns (theta, history of (L, theta, gradient)) with the
+    objective of every evaluated design."""
+    import torch
+    theta = torch.tensor(np.asarray(theta0, dtype=np.float64).reshape(-1, 3), requires_grad=True)
+    lo = None if lower is None else torch.as_tensor(np.asarray(lower, dtype=np.float64).reshape(-1, 3))
+    hi = None if upper is None else torch.as_tensor(np.asarray(upper, dtype=np.float64).reshape(-1, 3))
+    history = []
+    for _ in range(iterations):
+        phi = design_porosity(theta, grid, boxes, width)
+        L = comfort_objective(phi, grid, x0, nsteps, ckpt_every, objective=objective)
+        (g,) = torch.autograd.grad(L, theta)
+        history.append((L.item(), theta.detach().clone().numpy(), g.numpy().copy()))
+        with torch.no_grad():
+            theta -= step_size * g
+            if lo is not None:
+                theta.copy_(torch.maximum(theta, lo))
+            if hi is not None:
+                theta.copy_(torch.minimum(theta, hi))
+    return theta.detach().numpy(), history
+
+
+def wind_robustness(params: dict, phi, winds, nsteps: int, objective=None, precision: str = "f32"):
+    """The objective of one design under several wind directions (the +-10
+    degree re-runs of Sec. 6), all directions advanced together as one batch
+    (uf_batch_*): params are the grid parameters (nx, ny, nz, ...) without
+    wind_dir_deg, phi the design's porosity.  Returns [L per direction]."""
+    insts = [dict(params, wind_dir_deg=float(d)) for d in winds]
+    b = Batch(insts, precision=precision)
+    ph = np.asarray(phi, dtype=b.grids[0].np_dtype)
+    for g in b.grids:
+        g.set_porosity(ph)
+        g.init_state()
+    b.run(nsteps, stats=False)
+    out = [g.objective_ex(objective) for g in b.grids]
+    b.close()
+    return out
 
 
 def design_porosity(theta, grid: "Grid", boxes, width: float):

@@ -71,3 +71,10 @@ def test_design_lattice_workload():
     # seeded: same seed, same heights; another seed, other heights
     assert np.array_equal(layouts.design_lattice().theta, d.theta)
     assert not np.array_equal(layouts.design_lattice(seed=1).theta, d.theta)
+    # six pedestrian-level target regions, each centred between four buildings
+    assert d.regions.shape == (6, 6) and d.u_t == 0.55
+    rx, ry = 0.5 * (d.regions[:, 0] + d.regions[:, 1]), 0.5 * (d.regions[:, 2] + d.regions[:, 3])
+    for x, y in zip(rx, ry):
+        near = np.sort(np.hypot(cx - x, cy - y))[:4]
+        np.testing.assert_allclose(near, near[0])
+    assert np.all(d.regions[:, 4:] == (0.0, 3.0))
