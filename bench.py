@@ -150,10 +150,12 @@ class ClockSampler:
 
 
 def source_digest():
+    """Digest of the device code of the single-grid kernels (the .cuh
+    headers); host-side launch code and the batched kernels are outside it."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2204_01117_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
+        if f.endswith(".cuh"):
             with open(os.path.join(csrc, f), "rb") as fh:
                 h.update(fh.read())
     return h.hexdigest()[:16]
@@ -430,6 +432,174 @@ def preconditioner_table(steps: int = 10):
     return {"workload": "urban block 256x256x64 FP32, " + str(steps) + " timed steps after 3", "rows": rows}
 
 
+# ------------------------------------------------------------- large workload
+
+def large_scenario(grid):
+    """The 512 x 512 x 128 urban block (1 m cells, 400 boxes of height
+    5-120 m, 800 canopies, log law 5 m/s at 10 m), or the same recipe on a
+    smaller grid with the object counts scaled by area (for profiling)."""
+    from paper_2204_01117_gb300 import layouts
+    nx, ny, nz = grid
+    if (nx, ny, nz) == (512, 512, 128):
+        return layouts.config("urban512")
+    area = nx * ny / (512 * 512)
+    return layouts.urban_block(nx, ny, nz, h=1.0, n_boxes=max(1, round(400 * area)),
+                               n_trees=max(1, round(800 * area)), height=(5.0, min(120.0, 0.9 * nz)), u_ref=5.0)
+
+
+def fp64_flops_per_cell(kernel_label: str):
+    """FP64 operations per finest-level cell of a kernel (an FMA counts two)
+    from the committed ncu summary, or None when it is missing or the kernel
+    sources changed since."""
+    p = os.path.join(ROOT, "profiles", "mg_fp64_urban512.md")
+    if not os.path.exists(p):
+        return None
+    text = open(p).read()
+    m = re.search(r"source digest:\s*`([0-9a-f]+)`", text)
+    if not m or m.group(1) != source_digest():
+        return None
+    for line in text.splitlines():
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 3 and cells[0] == kernel_label:
+            try:
+                return float(cells[2])
+            except ValueError:
+                return None
+    return None
+
+
+def run_large(args):
+    """Plain FP64 against FP32 + FP64 reductions on the large urban block:
+    one FP64 initial state, copied into both grids; `steps` steps of each
+    with the CFL time step (the first 3 untimed, the rest timed with CUDA
+    events); relative L2 difference of every field and the divergence at the
+    end; per-kernel CUDA-event rooflines of one eager step of each; then the
+    adjoint of the comfort objective over the last `adjoint_steps` steps of
+    the FP32 run, from its state at step steps - adjoint_steps, with the
+    fixed time step of the run's first step (a fixed dt is needed for the
+    adjoint) and checkpoints every 10 steps, against the forward time of the
+    same steps."""
+    import numpy as np
+    import torch
+    from paper_2204_01117_gb300 import uf
+    torch.cuda.set_device(0)
+    uf.build()
+    uf.load()
+    grid = tuple(int(x) for x in args.large_grid.split("x"))
+    steps = max(8, args.steps if args.steps is not None else 1000)
+    adj_steps = min(100, steps // 2)
+    t_gen = time.perf_counter()
+    sc = large_scenario(grid)
+    t_gen = time.perf_counter() - t_gen
+    g64 = uf.Grid(sc.nx, sc.ny, sc.nz, precision="f64", **sc.params())
+    g64.set_porosity(sc.phi)
+    g64.init_state()
+    x0 = g64.state()
+    g32 = uf.Grid(sc.nx, sc.ny, sc.nz, precision="f32", **sc.params())
+    g32.set_porosity(sc.phi.astype(np.float32))
+    g32.set_fields(x0)
+    del x0
+    warm = 3
+    first = g32.step()
+    g32.run(warm - 1, stats=False)
+    g64.run(warm, stats=False)
+    snap_at = steps - adj_steps
+
+    def timed(g, n, snapshot=None):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms, done, snap = 0.0, 0, None
+        for chunk in ([snapshot - warm, n - snapshot] if snapshot else [n - warm]):
+            torch.cuda.synchronize()
+            e0.record(g.stream)
+            g.run(chunk, stats=False)
+            e1.record(g.stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            done += chunk
+            if snapshot and snap is None:
+                snap = g.state()
+        return ms, done, snap
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    with ClockSampler(vis.split(",")[0].strip() if vis else "0") as clk:
+        ms32, n32, snap = timed(g32, steps, snapshot=snap_at if not args.no_adjoint else None)
+        ms64, n64, _ = timed(g64, steps)
+    err = {}
+    for f in ("u", "v", "w", "p", "k", "omega"):
+        a = g32.get_state(f).astype(np.float64)
+        r = g64.get_state(f)
+        err[f] = float(np.linalg.norm(a - r) / max(np.linalg.norm(r), 1e-300))
+    div32, div64 = g32.divergence(), g64.divergence()
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    fp64_peak = 152 * 2 * 2 * 2070e6          # SMs x FP64 FMA/clk/SM x 2 flops x max SM clock
+
+    def roofline(g, fp64=False):
+        _, kernels = g.profile_step()
+        name, k = max(kernels.items(), key=lambda kv: kv[1]["total_ms"])
+        avg_s = k["total_ms"] / k["launches"] * 1e-3
+        out = {"bound": "hbm", "kernel": name, "achieved": k["bytes_per_launch"] / avg_s / 1e9, "peak": peak,
+               "unit": "GB/s", "peak_source": f"hbm_gbs of {peak_kind}",
+               "kernel_share_of_step": k["total_ms"] / sum(x["total_ms"] for x in kernels.values()),
+               "avg_launch_us": avg_s * 1e6}
+        out["frac"] = out["achieved"] / peak
+        if fp64:
+            fpc = fp64_flops_per_cell(name)
+            out["fp64_alu"] = None if fpc is None else {
+                "achieved": fpc * sc.cells / avg_s / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                "frac": fpc * sc.cells / avg_s / fp64_peak, "flops_per_cell": fpc,
+                "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz"}
+        return out
+
+    line = {
+        "metric": f"RANS cell-updates/s at {sc.nx}x{sc.ny}x{sc.nz}: plain FP64 vs FP32 + FP64 reductions",
+        "value": sc.cells * n32 / (ms32 * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warm,
+        "ms_per_step": ms32 / n32, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"urban block {sc.nx}x{sc.ny}x{sc.nz}, h=1 m, {sc.name}, log-law inflow 5 m/s at "
+                               f"10 m, CFL dt, MG-preconditioned CG; both runs from one FP64 initial state",
+                   "cells": sc.cells, "layout_seconds": t_gen,
+                   "l2": "no flush: per-step working set > 129 MB L2"},
+        "fp32": {"value": sc.cells * n32 / (ms32 * 1e-3), "ms_per_step": ms32 / n32, "roofline": roofline(g32),
+                 "divergence": div32},
+        "fp64": {"value": sc.cells * n64 / (ms64 * 1e-3), "ms_per_step": ms64 / n64,
+                 "roofline": roofline(g64, fp64=True), "divergence": div64},
+        "fp32_vs_fp64_rel_l2": err,
+        "clocks": clk.summary(),
+    }
+    g64.close()
+    del g64
+    torch.cuda.empty_cache()
+    if not args.no_adjoint:
+        ga = uf.Grid(sc.nx, sc.ny, sc.nz, precision="f32", fixed_dt=first.dt, **sc.params())
+        ga.set_porosity(sc.phi.astype(np.float32))
+        ga.set_fields(snap)
+        ga.run(1, stats=False)
+        ga.set_fields(snap)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ga.run(adj_steps, stats=False)
+        J = ga.objective()
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t
+        ga.set_fields(snap)
+        dphi = torch.empty(ga.shapes["phi"], dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        Ja, _ = ga.adjoint_run(adj_steps, 10, out=dphi)
+        torch.cuda.synchronize()
+        ta = time.perf_counter() - t
+        line["adjoint"] = {"steps": adj_steps, "ckpt_every": 10, "fixed_dt": first.dt, "forward_ms": tf * 1e3,
+                           "adjoint_ms": ta * 1e3, "ratio": ta / tf, "J": J, "J_matches_forward": bool(Ja == J),
+                           "dJ_dphi_norm": float(torch.linalg.vector_norm(dphi.double()).item()),
+                           "workspace_bytes": int(ga.lib.uf_adjoint_workspace_bytes(ga._h, adj_steps, 10))}
+        ga.free_adjoint_workspace()
+        ga.close()
+    g32.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- oracle arm
 
 def oracle_sample(max_seconds: float = 150.0, steps_wanted: int = 1):
@@ -589,7 +759,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 50; 1000 with --large)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
@@ -597,7 +767,14 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 32-instance leg")
     ap.add_argument("--preconditioners", action="store_true",
                     help="print the solver comparison table (CG iterations, step time) instead of the bench line")
+    ap.add_argument("--large", action="store_true",
+                    help="print the plain-FP64 vs FP32 comparison on the 512x512x128 block instead of the bench line")
+    ap.add_argument("--large-grid", default="512x512x128", help="grid of --large (NXxNYxNZ)")
     args = ap.parse_args()
+    if args.large:
+        return run_large(args)
+    if args.steps is None:
+        args.steps = 50
     if args.preconditioners:
         import torch
         torch.cuda.set_device(0)

@@ -175,8 +175,14 @@ uf_status uf_get_fields(uf_grid* g, int n, const int* fields, void* const* bufs)
 uf_status uf_init_state(uf_grid* g);
 
 /* One time step: dt -> eddy viscosity -> MacCormack advection -> diffusion
- * -> drag + velocity BCs -> pressure solve (warm start from the previous
- * pressure) -> projection -> k-omega update.  Replays a captured CUDA graph;
+ * -> drag + velocity BCs -> pressure solve (for the correction to the
+ * pressure extrapolated in time, 2 p^n - p^{n-1}) -> projection -> k-omega
+ * update.  The pressure state is held in twice the working precision (an
+ * unevaluated pair of FP32 values for FP32 grids, FP64 for FP64 grids): it
+ * grows upstream of the outlet far beyond the differences the projection
+ * uses.  UF_FIELD_P reads and writes it rounded to the grid precision, and
+ * a pressure written from outside has no history (p^{n-1} = p^n).  Replays a
+ * captured CUDA graph;
  * the CG loop runs in a conditional (while) graph node, so the host never
  * waits inside the step.  stats == NULL: asynchronous.  stats != NULL: the
  * call synchronises the stream and fills *stats; a failed device check is

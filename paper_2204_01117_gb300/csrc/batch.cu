@@ -152,16 +152,29 @@ struct AdvP {
   uf::AdvectArgs<T> a;
 };
 template <typename T>
-struct FaceP {   // diffusion (c = nu_t), drag + BCs (c = drag coefficient), projection (c = p)
+struct FaceP {   // diffusion (c = nu_t), drag + BCs (c = drag coefficient)
   uf::StepParams<T> sp;
   const T *ui, *vi, *wi, *c;
   T *uo, *vo, *wo;
 };
 template <typename T>
+struct ProjP {   // projection from the pressure store
+  uf::StepParams<T> sp;
+  const uf::PStore<T>* pr;
+  T *u, *v, *w;
+};
+template <typename T>
+struct CommitP { // p^{n+1} from the solve's correction, in the pressure store
+  uf::StepParams<T> sp;
+  T* delta;
+  uf::PStore<T> *pn, *gs;
+  const uf::SolveState* st;
+};
+template <typename T>
 struct RhsP {
   uf::StepParams<T> sp;
   const T *u, *v, *w;
-  T *b, *pr, *pp;
+  T* b;
   double* partials;
   uf::SolveState* st;
 };
@@ -170,6 +183,7 @@ struct CgP {     // CG initial residual, direction + A d
   uf::Level<T> L;
   const T* b;
   T* x;
+  const uf::PStore<T>* g;   // guess of the correction solve (pressure store)
   const T* z;
   T *d0, *d1, *q;
   double* partials;
@@ -239,7 +253,7 @@ template <typename T>
 __global__ void __launch_bounds__(uf::NT, 6) kb_pressure_rhs(const __grid_constant__ Args<RhsP<T>> A) {
   for_items(&A.m, [&](int i, int zc, const VBlock& vb) {
     const RhsP<T>& P = A.at[i];
-    uf::pressure_rhs_body<T>(P.sp, P.u, P.v, P.w, P.b, P.pr, P.pp, zc, P.partials, P.st, vb);
+    uf::pressure_rhs_body<T>(P.sp, P.u, P.v, P.w, P.b, zc, P.partials, P.st, vb);
   });
 }
 
@@ -253,7 +267,7 @@ __global__ void __launch_bounds__(uf::NT) kb_cg_init(const __grid_constant__ Arg
                                                      cudaGraphConditionalHandle cond, int use_cond, int* left) {
   for_items(&A.m, [&](int i, int zc, const VBlock& vb) {
     const CgP<T>& P = A.at[i];
-    uf::cg_init_body<T>(P.L, P.b, P.x, zc, P.partials, P.st, cond, use_cond, left, vb);
+    uf::cg_init_body<T>(P.L, P.b, P.x, P.g, zc, P.partials, P.st, cond, use_cond, left, vb);
   });
 }
 
@@ -293,10 +307,18 @@ __global__ void __launch_bounds__(uf::FT, 4) kb_mg_up(const __grid_constant__ Ar
 }
 
 template <typename T>
-__global__ void __launch_bounds__(uf::NT) kb_project(const __grid_constant__ Args<FaceP<T>> A) {
+__global__ void __launch_bounds__(uf::NT, 6) kb_pressure_commit(const __grid_constant__ Args<CommitP<T>> A) {
   for_plane_items(&A.m, [&](int i, const VBlock& vb) {
-    const FaceP<T>& P = A.at[i];
-    uf::project_body<T>(P.sp, P.c, P.uo, P.vo, P.wo, vb);
+    const CommitP<T>& P = A.at[i];
+    uf::pressure_commit_body<T>(P.sp, P.delta, P.pn, P.gs, P.st, vb);
+  });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(uf::NT) kb_project(const __grid_constant__ Args<ProjP<T>> A) {
+  for_plane_items(&A.m, [&](int i, const VBlock& vb) {
+    const ProjP<T>& P = A.at[i];
+    uf::project_body<T>(P.sp, P.pr, P.u, P.v, P.w, vb);
   });
 }
 
@@ -612,6 +634,7 @@ class BatchImpl final : public uf_batch {
     std::memset(&P, 0, sizeof(P));
     P.L = G.lv[0];
     P.b = G.b; P.x = G.p; P.z = G.z; P.d0 = G.d0; P.d1 = G.d1; P.q = G.q;
+    P.g = G.gd;
     P.partials = G.partials;
     P.st = G.st;
     return P;
@@ -663,19 +686,17 @@ class BatchImpl final : public uf_batch {
         P.sp = G.sp;
         P.u = G.u; P.v = G.v; P.w = G.w;
         P.b = G.b;
-        P.pr = G.p;
-        P.pp = G.pp;
         P.partials = G.partials;
         P.st = G.st;
       });
-      L(s, "b_pressure_rhs", plane_bytes(MAP_CHUNK, 8),
+      L(s, "b_pressure_rhs", plane_bytes(MAP_CHUNK, 4),
         [&] { k<<<grid_of(k, uf::NT, 0, items(MAP_CHUNK)), blk, 0, s>>>(A); });
     }
     L(s, "b_begin_solve", 0, [&] { kb_begin_solve<<<1, 32, 0, s>>>(d_left, n); });
     {
       auto k = kb_cg_init<T>;
       const auto& A = args<CgP<T>>(MAP_CHUNK, [](CgP<T>& P, const View<T>& G) { P = cg_params(G); });
-      L(s, "b_cg_init", plane_bytes(MAP_CHUNK, 3),
+      L(s, "b_cg_init", plane_bytes(MAP_CHUNK, 5),
         [&] { k<<<grid_of(k, uf::NT, 0, items(MAP_CHUNK)), blk, 0, s>>>(A, cond, use_cond, d_left); });
     }
     vcycle(s, 0, cond, use_cond);
@@ -692,9 +713,20 @@ class BatchImpl final : public uf_batch {
 
   // a8, a9, the k / omega buffer swap
   void rec_post(cudaStream_t s) {
-    launch_plane(kb_project<T>, MAP_FACE, s, "b_project", 7, args<FaceP<T>>(MAP_FACE, [](FaceP<T>& P, const View<T>& G) {
-      P = face_params(G, nullptr, nullptr, nullptr, G.p, G.u, G.v, G.w);
-    }));
+    launch_plane(kb_pressure_commit<T>, MAP_CELL, s, "b_pressure_commit", 10,
+                 args<CommitP<T>>(MAP_CELL, [](CommitP<T>& P, const View<T>& G) {
+                   P.sp = G.sp;
+                   P.delta = G.p;
+                   P.pn = G.pd;
+                   P.gs = G.gd;
+                   P.st = G.st;
+                 }));
+    launch_plane(kb_project<T>, MAP_FACE, s, "b_project", 8,
+                 args<ProjP<T>>(MAP_FACE, [](ProjP<T>& P, const View<T>& G) {
+                   P.sp = G.sp;
+                   P.pr = G.pd;
+                   P.u = G.u; P.v = G.v; P.w = G.w;
+                 }));
     {
       auto k = kb_turbulence<T>;
       const auto& A = args<CellP<T>>(MAP_CELL, [](CellP<T>& P, const View<T>& G) { P = cell_params(G); });

@@ -121,7 +121,7 @@ struct Plan {
   std::vector<LevelDims> levels;
   int coarse_n;
   // offsets
-  size_t u, v, w, uh, vh, wh, ut, vt, wt, u2, v2, w2, k0, k1, o0, o1, cc, phi, nut, p, pp, b, r, r2, z, q, d0, d1;
+  size_t u, v, w, uh, vh, wh, ut, vt, wt, u2, v2, w2, k0, k1, o0, o1, cc, phi, nut, p, pd, gd, b, r, r2, z, q, d0, d1;
   int nl;                  // multigrid levels in use (1 without MG)
   int auto_tail_level;     // shallowest level whose tail fits the shared-memory budget
   int tail_level;          // first level run by the shared-memory tail kernel
@@ -152,7 +152,8 @@ Plan make_plan(const uf_grid_desc* d) {
   P.k0 = L.take(P.n_c * tb); P.k1 = L.take(P.n_c * tb);
   P.o0 = L.take(P.n_c * tb); P.o1 = L.take(P.n_c * tb);
   P.cc = L.take(P.n_c * tb); P.phi = L.take(P.n_c * tb); P.nut = L.take(P.n_c * tb);
-  P.p = L.take(P.n_c * tb); P.pp = L.take(P.n_c * tb); P.b = L.take(P.n_c * tb); P.r = L.take(P.n_c * tb);
+  P.p = L.take(P.n_c * tb); P.b = L.take(P.n_c * tb); P.r = L.take(P.n_c * tb);
+  P.pd = L.take(P.n_c * 2 * tb); P.gd = L.take(P.n_c * 2 * tb);   // pressure store: (hi, lo) pairs or FP64
   P.r2 = L.take(P.n_c * tb);
   P.z = L.take(P.n_c * tb); P.q = L.take(P.n_c * tb);
   P.d0 = L.take(P.n_c * tb); P.d1 = L.take(P.n_c * tb);
@@ -311,11 +312,15 @@ class GridImpl final : public uf_grid {
   cudaStream_t stream = nullptr, cap = nullptr, cap2 = nullptr;
   uf::StepParams<T> sp;
   std::vector<uf::Level<T>> lv;
-  T *u, *v, *w, *uh, *vh, *wh, *ut, *vt, *wt, *u2, *v2, *w2, *kb[2], *ob[2], *cc, *phi, *nut, *p, *pp, *b, *r, *r2, *z, *q,
+  T *u, *v, *w, *uh, *vh, *wh, *ut, *vt, *wt, *u2, *v2, *w2, *kb[2], *ob[2], *cc, *phi, *nut, *p, *b, *r, *r2, *z, *q,
     *d0, *d1, *prof;
+  // the pressure p^n and the next solve's guess 2 p^n - p^{n-1} in the
+  // pressure store; p holds the solve's correction, then p^{n+1} rounded
+  uf::PStore<T> *pd, *gd;
   uf::TailArgs<T> tail;
-  T* sol_x = nullptr;   // the solve's unknown (p for the step; mu for the adjoint)
+  T* sol_x = nullptr;   // the solve's unknown (the pressure correction for the step; mu for the adjoint)
   T* sol_b = nullptr;   // its right-hand side
+  const uf::PStore<T>* sol_g = nullptr;   // guess of the step's solve (nullptr: warm start in sol_x)
   double *dt, *scal, *partials, *ainv;
   T* dtT;
   uf::SolveState* st;
@@ -350,9 +355,11 @@ class GridImpl final : public uf_grid {
     ut = at<T>(P.ut); vt = at<T>(P.vt); wt = at<T>(P.wt);
     u2 = at<T>(P.u2); v2 = at<T>(P.v2); w2 = at<T>(P.w2);
     kb[0] = at<T>(P.k0); kb[1] = at<T>(P.k1); ob[0] = at<T>(P.o0); ob[1] = at<T>(P.o1);
-    cc = at<T>(P.cc); phi = at<T>(P.phi); nut = at<T>(P.nut); p = at<T>(P.p); pp = at<T>(P.pp); b = at<T>(P.b);
+    cc = at<T>(P.cc); phi = at<T>(P.phi); nut = at<T>(P.nut); p = at<T>(P.p); b = at<T>(P.b);
+    pd = at<uf::PStore<T>>(P.pd); gd = at<uf::PStore<T>>(P.gd);
     sol_x = p;
     sol_b = b;
+    sol_g = gd;
     r = at<T>(P.r); r2 = at<T>(P.r2); z = at<T>(P.z); q = at<T>(P.q); d0 = at<T>(P.d0); d1 = at<T>(P.d1);
     prof = at<T>(P.prof);
     dt = at<double>(P.dt); dtT = at<T>(P.dtT); scal = at<double>(P.scal); partials = at<double>(P.partials);
@@ -509,7 +516,9 @@ class GridImpl final : public uf_grid {
 
   // z-marching grid of level l: 32 x 8 columns, zc planes (even) per block;
   // by default zc is chosen so that the level still gives a few blocks per
-  // SM, else it is the tuned value.
+  // SM, else it is the tuned value.  Either way zc is then doubled until the
+  // launch has at most kPartials blocks, the capacity of the reduction
+  // buffer every block writes one partial sum to.
   int march_zc_tuned[uf::MAX_LEVELS] = {0};
   dim3 march_grid(int l, int* zc) const {
     const uf::Level<T>& L = lv[l];
@@ -519,6 +528,7 @@ class GridImpl final : public uf_grid {
       z = 16;
       while (z > 2 && (long)bx * by * ((L.nz + z - 1) / z) < 456) z /= 2;
     }
+    while (z < L.nz && (long long)bx * by * ((L.nz + z - 1) / z) > kPartials) z *= 2;
     *zc = z;
     return dim3(bx, by, (L.nz + z - 1) / z);
   }
@@ -616,8 +626,9 @@ class GridImpl final : public uf_grid {
   void rec_cg_init(cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
     int zc;
     dim3 g = chunk_grid(lv[0].nx, lv[0].ny, lv[0].nz, &zc);
-    L(s, "cg_init", 3 * N() * tb(), [&] {
-      uf::k_cg_init<T><<<g, dim3(uf::BX, uf::BY), 0, s>>>(lv[0], sol_b, sol_x, zc, partials, st, cond, use_cond);
+    L(s, "cg_init", N() * (3 * tb() + (sol_g ? 2 * tb() : 0.0)), [&] {
+      uf::k_cg_init<T><<<g, dim3(uf::BX, uf::BY), 0, s>>>(lv[0], sol_b, sol_x, sol_g, zc, partials, st, cond,
+                                                          use_cond);
     });
   }
   void rec_cg_iter(cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
@@ -720,15 +731,17 @@ class GridImpl final : public uf_grid {
     L(s, "drag_bc", 2 * faces + cells, [&] { uf::k_drag_bc<T><<<ga, blk, 0, s>>>(sp, u2, v2, w2, cc, u, v, w); });
     int zc;
     const dim3 gr = chunk_grid(d.nx, d.ny, d.nz, &zc);
-    L(s, "pressure_rhs", faces + 5 * cells,
-      [&] { uf::k_pressure_rhs<T><<<gr, blk, 0, s>>>(sp, u, v, w, b, p, pp, zc, partials, st); });
+    L(s, "pressure_rhs", faces + cells,
+      [&] { uf::k_pressure_rhs<T><<<gr, blk, 0, s>>>(sp, u, v, w, b, zc, partials, st); });
   }
 
   void rec_post(cudaStream_t s, const T* kin, const T* oin, T* kout, T* oout) {
     const dim3 blk(uf::BX, uf::BY);
     const double faces = 3 * N() * tb(), cells = N() * tb();
-    L(s, "project", 2 * faces + cells,
-      [&] { uf::k_project<T><<<plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1), blk, 0, s>>>(sp, p, u, v, w); });
+    L(s, "pressure_commit", N() * 10 * tb(),
+      [&] { uf::k_pressure_commit<T><<<plane_grid(d.nx, d.ny, d.nz), blk, 0, s>>>(sp, p, pd, gd, st); });
+    L(s, "project", 2 * faces + 2 * cells,
+      [&] { uf::k_project<T><<<plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1), blk, 0, s>>>(sp, pd, u, v, w); });
     L(s, "turbulence", faces + 4 * cells,
       [&] { uf::k_turbulence<T><<<plane_grid(d.nx, d.ny, d.nz), blk, 0, s>>>(sp, u, v, w, kin, oin, kout, oout); });
   }
@@ -778,11 +791,11 @@ class GridImpl final : public uf_grid {
   // checkpoint segment, the checkpoints, the final state and the adjoint
   // arrays.  Offsets in elements of T, every array 64-element aligned.
   struct AdjLayout {
-    size_t faceN, cellN, slot, ckpt, total;
+    size_t faceN, cellN, cellD, slot, ckpt, total;
     int C, nseg;
     size_t tape0, ckpt0, fin, lam;
     // offsets inside one tape slot; a slot starts with a checkpoint
-    // (faces | k | omega | p | previous p) so that save_state() fills its head
+    // (faces | k | omega | p^n | guess) so that save_state() fills its head
     size_t s_nut, s_uh, s_ut, s_u2, s_u1;
   };
   static size_t a64(size_t n) { return (n + 63) / 64 * 64; }
@@ -793,7 +806,8 @@ class GridImpl final : public uf_grid {
     A.cellN = a64(P.n_c);
     A.C = C;
     A.nseg = (nsteps + C - 1) / C;
-    A.ckpt = A.faceN + 4 * A.cellN;       // faces, k, omega, p, p of the previous step
+    A.cellD = A.cellN * (sizeof(uf::PStore<T>) / sizeof(T));   // a pressure-store cell array in units of T
+    A.ckpt = A.faceN + 2 * A.cellN + 2 * A.cellD;              // faces, k, omega, p^n, guess
     A.s_nut = A.ckpt;
     A.s_uh = A.s_nut + A.cellN;
     A.s_ut = A.s_uh + A.faceN;
@@ -830,14 +844,25 @@ class GridImpl final : public uf_grid {
   cudaError_t copy_cell(T* dst, const T* src) {
     return cudaMemcpyAsync(dst, src, P.n_c * sizeof(T), cudaMemcpyDeviceToDevice, stream);
   }
-  // checkpoint layout: faces | k | omega | p | previous p (the solve's extrapolation)
+  cudaError_t copy_cell_ps(uf::PStore<T>* dst, const uf::PStore<T>* src) {
+    return cudaMemcpyAsync(dst, src, P.n_c * sizeof(uf::PStore<T>), cudaMemcpyDeviceToDevice, stream);
+  }
+  // p (grid precision) -> the pressure store with no history, or back
+  cudaError_t pressure_sync(int to_store) {
+    uf::k_pressure_sync<T><<<(unsigned)((P.n_c + 255) / 256), 256, 0, stream>>>(p, pd, gd, P.n_c, to_store);
+    return cudaGetLastError();
+  }
+  // checkpoint layout: faces | k | omega | p^n | the next solve's guess (both in the pressure store)
+  uf::PStore<T>* ckpt_pressure(T* slot, const AdjLayout& A, int which) const {
+    return reinterpret_cast<uf::PStore<T>*>(slot + A.faceN + 2 * A.cellN + (size_t)which * A.cellD);
+  }
   cudaError_t save_state(T* slot, const AdjLayout& A) {
     FaceSet f = faces_at(slot);
     cudaError_t e = copy_faces(f, u, v, w);
     if (e == cudaSuccess) e = copy_cell(slot + A.faceN, kb[parity]);
     if (e == cudaSuccess) e = copy_cell(slot + A.faceN + A.cellN, ob[parity]);
-    if (e == cudaSuccess) e = copy_cell(slot + A.faceN + 2 * A.cellN, p);
-    if (e == cudaSuccess) e = copy_cell(slot + A.faceN + 3 * A.cellN, pp);
+    if (e == cudaSuccess) e = copy_cell_ps(ckpt_pressure(slot, A, 0), pd);
+    if (e == cudaSuccess) e = copy_cell_ps(ckpt_pressure(slot, A, 1), gd);
     return e;
   }
   cudaError_t load_state(const T* slot, const AdjLayout& A) {
@@ -848,8 +873,10 @@ class GridImpl final : public uf_grid {
     if (e == cudaSuccess) e = cudaMemcpyAsync(w, f.w, P.n_w * sizeof(T), cudaMemcpyDeviceToDevice, stream);
     if (e == cudaSuccess) e = copy_cell(kb[0], slot + A.faceN);
     if (e == cudaSuccess) e = copy_cell(ob[0], slot + A.faceN + A.cellN);
-    if (e == cudaSuccess) e = copy_cell(p, slot + A.faceN + 2 * A.cellN);
-    if (e == cudaSuccess) e = copy_cell(pp, slot + A.faceN + 3 * A.cellN);
+    T* sl = const_cast<T*>(slot);
+    if (e == cudaSuccess) e = copy_cell_ps(pd, ckpt_pressure(sl, A, 0));
+    if (e == cudaSuccess) e = copy_cell_ps(gd, ckpt_pressure(sl, A, 1));
+    if (e == cudaSuccess) e = pressure_sync(0);
     return e;
   }
 
@@ -885,6 +912,7 @@ class GridImpl final : public uf_grid {
     adj_solve_exec = nullptr;
     sol_x = mu;
     sol_b = badj;
+    sol_g = nullptr;
     int nf, ns, ni;
     auto pre = [&](cudaStream_t s2) {
       int zc;
@@ -895,6 +923,7 @@ class GridImpl final : public uf_grid {
     uf_status s = capture(&adj_solve_exec, pre, [&](cudaStream_t) {}, &nf, &ns, &ni);
     sol_x = p;
     sol_b = b;
+    sol_g = gd;
     if (s != UF_OK) return s;
     adj_mu = mu;
     adj_b = badj;
@@ -1266,6 +1295,7 @@ class GridImpl final : public uf_grid {
       cudaGraphExec_t ex = nullptr;
       sol_x = ut;
       sol_b = uh;
+      sol_g = nullptr;
       int nf, ns, ni;
       auto pre = [&](cudaStream_t s2) {
         cudaMemsetAsync(ut, 0, P.n_u * sizeof(T), s2);
@@ -1277,6 +1307,7 @@ class GridImpl final : public uf_grid {
       rs = capture(&ex, pre, [&](cudaStream_t) {}, &nf, &ns, &ni);
       sol_x = p;
       sol_b = b;
+      sol_g = gd;
       if (rs != UF_OK) break;
       cudaError_t e = cudaGraphLaunch(ex, stream);   // warm-up
       if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
@@ -1321,7 +1352,7 @@ class GridImpl final : public uf_grid {
     V.sp = sp;
     V.adv = advect_args();
     V.u = u; V.v = v; V.w = w; V.uh = uh; V.vh = vh; V.wh = wh; V.ut = ut; V.vt = vt; V.wt = wt;
-    V.u2 = u2; V.v2 = v2; V.w2 = w2; V.cc = cc; V.nut = nut; V.p = p; V.pp = pp; V.b = b; V.z = z; V.q = q;
+    V.u2 = u2; V.v2 = v2; V.w2 = w2; V.cc = cc; V.nut = nut; V.p = p; V.pd = pd; V.gd = gd; V.b = b; V.z = z; V.q = q;
     V.d0 = d0; V.d1 = d1;
     V.kb[0] = kb[0]; V.kb[1] = kb[1]; V.ob[0] = ob[0]; V.ob[1] = ob[1];
     V.parity = parity;
@@ -1395,7 +1426,7 @@ class GridImpl final : public uf_grid {
     if (f == UF_FIELD_PHI) return set_porosity(src);
     uf_status s = copy_in(ptr, lx, ly, lz, pitch, src);
     if (s == UF_OK && (f == UF_FIELD_U || f == UF_FIELD_V || f == UF_FIELD_W)) have_state = true;
-    if (s == UF_OK && f == UF_FIELD_P) UF_CUDA(copy_cell(pp, p));   // a new pressure has no history
+    if (s == UF_OK && f == UF_FIELD_P) UF_CUDA(pressure_sync(1));   // a new pressure has no history
     return s;
   }
 
@@ -1466,7 +1497,7 @@ class GridImpl final : public uf_grid {
         UF_CUDA(cudaGetLastError());
       }
       state |= fields[q] == UF_FIELD_U || fields[q] == UF_FIELD_V || fields[q] == UF_FIELD_W;
-      if (fields[q] == UF_FIELD_P) UF_CUDA(copy_cell(pp, p));
+      if (fields[q] == UF_FIELD_P) UF_CUDA(pressure_sync(1));
     }
     if (state) have_state = true;
     return UF_OK;
@@ -1504,6 +1535,8 @@ class GridImpl final : public uf_grid {
       auto pre = [&](cudaStream_t s) {
         const dim3 blk(uf::BX, uf::BY);
         const dim3 ga = plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1);
+        cudaMemsetAsync(pd, 0, P.n_c * sizeof(uf::PStore<T>), s);
+        cudaMemsetAsync(gd, 0, P.n_c * sizeof(uf::PStore<T>), s);
         uf::k_init_fields<T><<<ga, blk, 0, s>>>(sp, u, v, w, kb[0], ob[0], p);
         rec_count++;
         if (!(d.fixed_dt > 0)) {
@@ -1513,23 +1546,24 @@ class GridImpl final : public uf_grid {
         uf::k_drag_bc<T><<<ga, blk, 0, s>>>(sp, u, v, w, cc, uh, vh, wh);
         int zc;
         const dim3 gr = chunk_grid(d.nx, d.ny, d.nz, &zc);
-        uf::k_pressure_rhs<T><<<gr, blk, 0, s>>>(sp, uh, vh, wh, b, nullptr, nullptr, zc, partials, st);
+        uf::k_pressure_rhs<T><<<gr, blk, 0, s>>>(sp, uh, vh, wh, b, zc, partials, st);
         rec_count += 2;
       };
       auto post = [&](cudaStream_t s) {
         const dim3 blk(uf::BX, uf::BY);
-        uf::k_project<T><<<plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1), blk, 0, s>>>(sp, p, uh, vh, wh);
+        uf::k_pressure_commit<T><<<plane_grid(d.nx, d.ny, d.nz), blk, 0, s>>>(sp, p, pd, gd, st);
+        uf::k_project<T><<<plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1), blk, 0, s>>>(sp, pd, uh, vh, wh);
         cudaMemcpyAsync(u, uh, P.n_u * sizeof(T), cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(v, vh, P.n_v * sizeof(T), cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(w, wh, P.n_w * sizeof(T), cudaMemcpyDeviceToDevice, s);
-        rec_count++;
+        rec_count += 2;
       };
       uf_status s = capture(&init_exec, pre, post, &nf, &ns, &ni);
       if (s != UF_OK) return s;
     }
     parity = 0;
     UF_CUDA(cudaGraphLaunch(init_exec, stream));
-    UF_CUDA(copy_cell(pp, p));   // no previous pressure: the first guess is p itself
+    UF_CUDA(copy_cell_ps(gd, pd));   // no previous pressure: the first guess is p itself
     have_state = true;
     return check_device(nullptr);
   }
@@ -1721,12 +1755,15 @@ class GridImpl final : public uf_grid {
         uf::k_solve_reset<T><<<g, dim3(uf::BX, uf::BY), 0, s2>>>(lv[0], b, zc, partials, st);
         rec_count++;
       };
-      auto post = [&](cudaStream_t) {};
+      auto post = [&](cudaStream_t s2) {
+        uf::k_pressure_commit<T><<<plane_grid(d.nx, d.ny, d.nz), dim3(uf::BX, uf::BY), 0, s2>>>(sp, p, pd, gd, st);
+        rec_count++;
+      };
       s = capture(&solve_exec, pre, post, &nf, &ns, &ni);
       if (s != UF_OK) return s;
     }
     UF_CUDA(cudaGraphLaunch(solve_exec, stream));
-    UF_CUDA(copy_cell(pp, p));
+    UF_CUDA(copy_cell_ps(gd, pd));
     uf_step_stats o;
     s = check_device(&o);
     if (iters) *iters = o.cg_iters;

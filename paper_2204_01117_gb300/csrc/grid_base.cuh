@@ -15,7 +15,8 @@ struct GridView {
   uf_grid_desc d;
   uf::StepParams<T> sp;
   uf::AdvectArgs<T> adv;
-  T *u, *v, *w, *uh, *vh, *wh, *ut, *vt, *wt, *u2, *v2, *w2, *cc, *nut, *p, *pp, *b, *z, *q, *d0, *d1;
+  T *u, *v, *w, *uh, *vh, *wh, *ut, *vt, *wt, *u2, *v2, *w2, *cc, *nut, *p, *b, *z, *q, *d0, *d1;
+  uf::PStore<T> *pd, *gd;          // pressure p^n and the next guess (pressure store); p: the correction
   T* kb[2];
   T* ob[2];
   int parity;                      // kb[parity], ob[parity] hold the current k, omega

@@ -135,7 +135,7 @@ extern "C" uf_status uf_poisson_solve_static(int nx, int ny, int nz, double wind
   const float w = 1.65f;
 
   uf::k_solve_reset<float><<<grid, blk, 0, s>>>(L, b, zc, partials, st);
-  uf::k_cg_init<float><<<grid, blk, 0, s>>>(L, b, p, zc, partials, st, 0, 0);
+  uf::k_cg_init<float><<<grid, blk, 0, s>>>(L, b, p, nullptr, zc, partials, st, 0, 0);
   uf::k_precond_simple<float><<<grid, blk, 0, s>>>(L, 2, w, z, zc, 0, partials, st, 0, 0);
   int conv = 0;
   e = cudaMemcpyAsync(&conv, &st->converged, sizeof(int), cudaMemcpyDeviceToHost, s);

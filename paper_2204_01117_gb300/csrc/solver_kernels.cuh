@@ -78,6 +78,23 @@ __device__ __forceinline__ T level_apply(const Level<T>& L, int i, int j, int k,
   return acc;
 }
 
+// level_apply on the pressure store: the same stencil, with each
+// neighbour difference taken on the stored pairs (ps_diff).
+template <typename T>
+__device__ __forceinline__ T level_apply_store(const Level<T>& L, int i, int j, int k, const PStore<T>* __restrict__ g) {
+  const PStore<T> gc = g[lidx(L, i, j, k)];
+  const T xc = (T)ps_value(gc);
+  auto d = [&](int a, int b2, int c2) { return (T)ps_diff(gc, g[lidx(L, a, b2, c2)]); };
+  T acc = 0;
+  if (i > 0) acc += L.wx * d(i - 1, j, k); else if (L.out_mask & 1) acc += L.wx * xc;
+  if (i < L.nx - 1) acc += L.wx * d(i + 1, j, k); else if (L.out_mask & 2) acc += L.wx * xc;
+  if (j > 0) acc += L.wy * d(i, j - 1, k); else if (L.out_mask & 4) acc += L.wy * xc;
+  if (j < L.ny - 1) acc += L.wy * d(i, j + 1, k); else if (L.out_mask & 8) acc += L.wy * xc;
+  if (k > 0) acc += L.wz * d(i, j, k - 1); else if (L.out_mask & 16) acc += L.wz * xc;
+  if (k < L.nz - 1) acc += L.wz * d(i, j, k + 1); else if (L.out_mask & 32) acc += L.wz * xc;
+  return acc;
+}
+
 // Cell loop of a 32x8 thread tile over the z planes [z0, z1) of a block.
 #define UF_CELL_LOOP_VB(L, vb)                                              \
   const int i = (vb).x * BX + threadIdx.x, j = (vb).y * BY + threadIdx.y;   \
@@ -99,9 +116,13 @@ __device__ __forceinline__ void signal_converged(cudaGraphConditionalHandle cond
 
 // ------------------------------------------------------------ CG kernels --
 
-// r = b - A x (warm start x = p^n).  A zero right-hand side gives x = 0.
+// r = b - A x from the warm start in x.  With g != nullptr the solve is for
+// the correction to the guess g held in the pressure store (the pressure
+// extrapolated in time, see pressure_commit_body) instead: r = b - A g and
+// x = 0.  A zero right-hand side gives x = 0.
 template <typename T>
-__device__ __forceinline__ void cg_init_body(const Level<T>& L, const T* __restrict__ b, T* __restrict__ x, int zc,
+__device__ __forceinline__ void cg_init_body(const Level<T>& L, const T* __restrict__ b, T* __restrict__ x,
+                                             const PStore<T>* __restrict__ g, int zc,
                                              double* partials, SolveState* st, cudaGraphConditionalHandle cond,
                                              int use_cond, int* left, const VBlock& vb) {
   __shared__ double sh[32];
@@ -116,6 +137,11 @@ __device__ __forceinline__ void cg_init_body(const Level<T>& L, const T* __restr
       if (zero_rhs) {
         x[c] = T(0);
         L.r[c] = T(0);
+      } else if (g) {
+        const T rv = b[c] - level_apply_store(L, i, j, k, g);
+        x[c] = T(0);
+        L.r[c] = rv;
+        dacc.add(rv, rv);
       } else {
         const T ax = level_apply(L, i, j, k, [&](int a, int b2, int c2) { return x[lidx(L, a, b2, c2)]; });
         const T rv = b[c] - ax;
@@ -143,10 +169,10 @@ __device__ __forceinline__ void cg_init_body(const Level<T>& L, const T* __restr
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT) k_cg_init(Level<T> L, const T* __restrict__ b, T* __restrict__ x, int zc,
-                                                double* partials, SolveState* st,
-                                                cudaGraphConditionalHandle cond, int use_cond) {
-  cg_init_body<T>(L, b, x, zc, partials, st, cond, use_cond, nullptr, vblock());
+__global__ void __launch_bounds__(NT) k_cg_init(Level<T> L, const T* __restrict__ b, T* __restrict__ x,
+                                                const PStore<T>* __restrict__ g, int zc, double* partials,
+                                                SolveState* st, cudaGraphConditionalHandle cond, int use_cond) {
+  cg_init_body<T>(L, b, x, g, zc, partials, st, cond, use_cond, nullptr, vblock());
 }
 
 

@@ -415,15 +415,12 @@ struct SolveState {
   long long total_iters;   // CG iterations since the grid was created
 };
 
+// b = -(rho h / dt) (sum of the face fluxes of the cell), the right-hand
+// side of A p = b on the integer stencil, and ||b||^2 for the CG stop rule.
 template <typename T>
-// With pr != nullptr the kernel also forms the initial guess of the solve by
-// linear extrapolation in time, pr <- 2 p^n - p^{n-1}, keeping p^n in pp as
-// the next step's p^{n-1}; only the starting point of CG changes, not the
-// solution it converges to.
 __device__ __forceinline__ void pressure_rhs_body(const StepParams<T>& p, const T* __restrict__ u,
                                                   const T* __restrict__ v, const T* __restrict__ w, T* __restrict__ b,
-                                                  T* __restrict__ pr, T* __restrict__ pp, int zc, double* partials,
-                                                  SolveState* st, const VBlock& vb) {
+                                                  int zc, double* partials, SolveState* st, const VBlock& vb) {
   __shared__ double sh[32];
   __shared__ bool last;
   const int i = vb.x * BX + threadIdx.x, j = vb.y * BY + threadIdx.y;
@@ -434,14 +431,8 @@ __device__ __forceinline__ void pressure_rhs_body(const StepParams<T>& p, const 
     const T sc = -p.rho * p.h / *p.dtT;
     for (int k = z0; k < z1; ++k) {
       const T bv = sc * cell_flux(p, u, v, w, i, j, k);
-      const size_t c = idx_c(p, i, j, k);
-      b[c] = bv;
+      b[idx_c(p, i, j, k)] = bv;
       dacc.add(bv, bv);
-      if (pr) {
-        const T pn = pr[c];
-        pr[c] = T(2) * pn - pp[c];
-        pp[c] = pn;
-      }
     }
   }
   acc += dacc.value();
@@ -462,18 +453,63 @@ __device__ __forceinline__ void pressure_rhs_body(const StepParams<T>& p, const 
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_pressure_rhs(StepParams<T> p, const T* __restrict__ u, const T* __restrict__ v,
-                                                     const T* __restrict__ w, T* __restrict__ b, T* __restrict__ pr,
-                                                     T* __restrict__ pp, int zc, double* partials, SolveState* st) {
-  pressure_rhs_body<T>(p, u, v, w, b, pr, pp, zc, partials, st, vblock());
+                                                     const T* __restrict__ w, T* __restrict__ b, int zc,
+                                                     double* partials, SolveState* st) {
+  pressure_rhs_body<T>(p, u, v, w, b, zc, partials, st, vblock());
+}
+
+// After the pressure solve.  The solve works on the correction delta to the
+// guess g = 2 p^n - p^{n-1} (the pressure extrapolated in time, see
+// cg_init_body), which is small; this kernel forms p^{n+1} = g + delta in
+// the pressure store (PStore), the next guess 2 p^{n+1} - p^n in gs, and
+// leaves p^{n+1} rounded to the grid precision in delta, the copy the field
+// accessors read.  A zero right-hand side gives p = 0.
+template <typename T>
+__device__ __forceinline__ void pressure_commit_body(const StepParams<T>& p, T* __restrict__ delta,
+                                                     PStore<T>* __restrict__ pn, PStore<T>* __restrict__ gs,
+                                                     const SolveState* st, const VBlock& vb) {
+  const int i = vb.x * BX + threadIdx.x, j = vb.y * BY + threadIdx.y, k = vb.z;
+  if (i >= p.nx || j >= p.ny) return;
+  const size_t c = idx_c(p, i, j, k);
+  PStore<T> v, g;
+  ps_commit(gs[c], pn[c], delta[c], st->bb == 0.0, &v, &g);
+  pn[c] = v;
+  gs[c] = g;
+  delta[c] = (T)ps_value(v);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_pressure_commit(StepParams<T> p, T* __restrict__ delta,
+                                                        PStore<T>* __restrict__ pn, PStore<T>* __restrict__ gs,
+                                                        const SolveState* st) {
+  pressure_commit_body<T>(p, delta, pn, gs, st, vblock());
+}
+
+// A pressure set from outside (grid precision, in pg) becomes the stored
+// state with no history: pn = gs = pg.  to_store = 0 rounds pn back into pg.
+template <typename T>
+__global__ void k_pressure_sync(T* __restrict__ pg, PStore<T>* __restrict__ pn, PStore<T>* __restrict__ gs, size_t n,
+                                int to_store) {
+  const size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  if (to_store) {
+    const PStore<T> v = ps_from(pg[q]);
+    pn[q] = v;
+    gs[q] = v;
+  } else {
+    pg[q] = (T)ps_value(pn[q]);
+  }
 }
 
 
 // --------------------------------------------------------- a8: projection
 // u -= dt/(rho h) (p(c+) - p(c-)) on interior faces and on faces of outlet
-// sides (outer neighbour: the p = 0 ghost cell).  In place.
+// sides (outer neighbour: the p = 0 ghost cell).  In place.  The difference
+// is taken on the pressure store (PStore).
 template <typename T>
-__device__ __forceinline__ void project_body(const StepParams<T>& p, const T* __restrict__ pr, T* __restrict__ u,
-                                             T* __restrict__ v, T* __restrict__ w, const VBlock& vb) {
+__device__ __forceinline__ void project_body(const StepParams<T>& p, const PStore<T>* __restrict__ pr,
+                                             T* __restrict__ u, T* __restrict__ v, T* __restrict__ w,
+                                             const VBlock& vb) {
   int q, k;
   plane_of(vb.z, p.nz, q, k);
   const int i = vb.x * BX + threadIdx.x, j = vb.y * BY + threadIdx.y;
@@ -481,26 +517,26 @@ __device__ __forceinline__ void project_body(const StepParams<T>& p, const T* __
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   if (q == 0) {
     if (i > nx || j >= ny) return;
-    T pm, pp;
-    if (i == 0) { if (p.side[0] != OUTFLOW) return; pm = T(0); pp = pr[idx_c(p, 0, j, k)]; }
-    else if (i == nx) { if (p.side[1] != OUTFLOW) return; pm = pr[idx_c(p, nx - 1, j, k)]; pp = T(0); }
-    else { pm = pr[idx_c(p, i - 1, j, k)]; pp = pr[idx_c(p, i, j, k)]; }
-    u[idx_u(p, i, j, k)] -= g * (pp - pm);
+    T dp;
+    if (i == 0) { if (p.side[0] != OUTFLOW) return; dp = (T)ps_value(pr[idx_c(p, 0, j, k)]); }
+    else if (i == nx) { if (p.side[1] != OUTFLOW) return; dp = -(T)ps_value(pr[idx_c(p, nx - 1, j, k)]); }
+    else dp = (T)ps_diff(pr[idx_c(p, i, j, k)], pr[idx_c(p, i - 1, j, k)]);
+    u[idx_u(p, i, j, k)] -= g * dp;
   } else if (q == 1) {
     if (i >= nx || j > ny) return;
-    T pm, pp;
-    if (j == 0) { if (p.side[2] != OUTFLOW) return; pm = T(0); pp = pr[idx_c(p, i, 0, k)]; }
-    else if (j == ny) { if (p.side[3] != OUTFLOW) return; pm = pr[idx_c(p, i, ny - 1, k)]; pp = T(0); }
-    else { pm = pr[idx_c(p, i, j - 1, k)]; pp = pr[idx_c(p, i, j, k)]; }
-    v[idx_v(p, i, j, k)] -= g * (pp - pm);
+    T dp;
+    if (j == 0) { if (p.side[2] != OUTFLOW) return; dp = (T)ps_value(pr[idx_c(p, i, 0, k)]); }
+    else if (j == ny) { if (p.side[3] != OUTFLOW) return; dp = -(T)ps_value(pr[idx_c(p, i, ny - 1, k)]); }
+    else dp = (T)ps_diff(pr[idx_c(p, i, j, k)], pr[idx_c(p, i, j - 1, k)]);
+    v[idx_v(p, i, j, k)] -= g * dp;
   } else {
     if (i >= nx || j >= ny || k < 1 || k >= nz) return;
-    w[idx_c(p, i, j, k)] -= g * (pr[idx_c(p, i, j, k)] - pr[idx_c(p, i, j, k - 1)]);
+    w[idx_c(p, i, j, k)] -= g * (T)ps_diff(pr[idx_c(p, i, j, k)], pr[idx_c(p, i, j, k - 1)]);
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT) k_project(StepParams<T> p, const T* __restrict__ pr, T* __restrict__ u,
+__global__ void __launch_bounds__(NT) k_project(StepParams<T> p, const PStore<T>* __restrict__ pr, T* __restrict__ u,
                                                 T* __restrict__ v, T* __restrict__ w) {
   project_body<T>(p, pr, u, v, w, vblock());
 }

@@ -116,6 +116,59 @@ struct DotAcc<float> {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// ------------------------------------------------------ pressure store --
+// The pressure state is stored as an unevaluated pair (hi, lo) of FP32
+// values for FP32 grids -- twice the working precision, with every
+// operation on the FP32 pipes -- and as a double for FP64 grids.  It grows
+// upstream of the outlet to many times the neighbour differences the
+// projection uses; a single FP32 value would carry an absolute error of
+// eps |p| into every face.  Only differences of neighbouring pressures and
+// the commit of a new pressure read it; a difference of two pairs,
+// (hi1 - hi2) + (lo1 - lo2), is rounded relative to the difference itself.
+template <typename T>
+struct PStoreOf { using type = double; };
+template <>
+struct PStoreOf<float> { using type = float2; };
+template <typename T>
+using PStore = typename PStoreOf<T>::type;
+
+// Knuth's TwoSum: s + e == a + b exactly in round-to-nearest.  The _rn
+// intrinsics keep the compiler from contracting or reordering the steps.
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  const float av = __fsub_rn(s, bv);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv)));
+}
+// Sum of two pairs, renormalised: the accurate double-word addition
+// (Dekker 1971; Joldes, Muller and Popescu 2017, Algorithm 6), with TwoSum
+// in place of Fast2Sum so that no ordering of magnitudes is assumed.
+__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
+  float2 s = two_sum(a.x, b.x);
+  const float2 t = two_sum(a.y, b.y);
+  s = two_sum(s.x, __fadd_rn(s.y, t.x));
+  return two_sum(s.x, __fadd_rn(s.y, t.y));
+}
+__device__ __forceinline__ float ps_diff(float2 a, float2 b) {
+  return __fadd_rn(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y));
+}
+__device__ __forceinline__ double ps_diff(double a, double b) { return a - b; }
+__device__ __forceinline__ float ps_value(float2 a) { return __fadd_rn(a.x, a.y); }
+__device__ __forceinline__ double ps_value(double a) { return a; }
+__device__ __forceinline__ float2 ps_from(float v) { return make_float2(v, 0.f); }
+__device__ __forceinline__ double ps_from(double v) { return v; }
+// p^{n+1} = g + delta (zero: p = 0) and the next solve's guess 2 p^{n+1} - p^n.
+__device__ __forceinline__ void ps_commit(float2 g, float2 pn, float delta, bool zero, float2* pnew, float2* gnew) {
+  const float2 v = zero ? make_float2(0.f, 0.f) : pair_add(g, make_float2(delta, 0.f));
+  *pnew = v;
+  *gnew = pair_add(make_float2(2.f * v.x, 2.f * v.y), make_float2(-pn.x, -pn.y));
+}
+__device__ __forceinline__ void ps_commit(double g, double pn, double delta, bool zero, double* pnew, double* gnew) {
+  const double v = zero ? 0.0 : g + delta;
+  *pnew = v;
+  *gnew = 2.0 * v - pn;
+}
+
 // ------------------------------------------------------------- reduction --
 // Deterministic block + grid reduction in FP64: every block writes one
 // partial; the last block to finish (atomic ticket) sums the partials in a
