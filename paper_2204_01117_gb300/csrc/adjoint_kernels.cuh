@@ -507,15 +507,16 @@ __global__ void __launch_bounds__(NT) k_eddy_viscosity_adj(StepParams<T> p, cons
 // lam * weight into lF when lF != nullptr.  The gradient along a clamped
 // axis is zero.
 template <typename T>
-__device__ __forceinline__ void sample_adj(const T* __restrict__ F, T* lF, Lattice L, T a, T b, T c, T lam, T grad[3]) {
-  const bool fa = L.Lx >= 2 && a >= T(0) && a <= T(L.Lx - 1);
-  const bool fb = L.Ly >= 2 && b >= T(0) && b <= T(L.Ly - 1);
-  const bool fc = L.Lz >= 2 && c >= T(0) && c <= T(L.Lz - 1);
+__device__ __forceinline__ void sample_adj(const T* __restrict__ F, T* lF, Lattice L, int ia, T oa, int ib, T ob,
+                                           int ic, T oc, T lam, T grad[3]) {
+  const bool fa = L.Lx >= 2 && axis_inside(ia, oa, L.Lx);
+  const bool fb = L.Ly >= 2 && axis_inside(ib, ob, L.Ly);
+  const bool fc = L.Lz >= 2 && axis_inside(ic, oc, L.Lz);
   int i0, i1, j0, j1, k0, k1;
   T ta, tb, tc;
-  axis_cell(a, L.Lx, i0, i1, ta);
-  axis_cell(b, L.Ly, j0, j1, tb);
-  axis_cell(c, L.Lz, k0, k1, tc);
+  axis_cell(ia, oa, L.Lx, i0, i1, ta);
+  axis_cell(ib, ob, L.Ly, j0, j1, tb);
+  axis_cell(ic, oc, L.Lz, k0, k1, tc);
   const size_t r00 = (size_t)L.P * ((size_t)j0 + (size_t)L.Ly * k0);
   const size_t r10 = (size_t)L.P * ((size_t)j1 + (size_t)L.Ly * k0);
   const size_t r01 = (size_t)L.P * ((size_t)j0 + (size_t)L.Ly * k1);
@@ -547,15 +548,15 @@ __device__ __forceinline__ void displacement_adj(const AdvectArgs<T>& A, int q, 
                                                  T* lu, T* lv, T* lw) {
   if (q == 0) {
     aadd(&lu[(size_t)i + (size_t)A.Lu.P * ((size_t)j + (size_t)A.Lu.Ly * k)], s * ld[0]);
-    sample_adj<T>(A.v, lv, A.Lv, T(i) - T(0.5), T(j) + T(0.5), T(k), s * ld[1], nullptr);
-    sample_adj<T>(A.w, lw, A.Lw, T(i) - T(0.5), T(j), T(k) + T(0.5), s * ld[2], nullptr);
+    sample_adj<T>(A.v, lv, A.Lv, i, T(-0.5), j, T(0.5), k, T(0), s * ld[1], nullptr);
+    sample_adj<T>(A.w, lw, A.Lw, i, T(-0.5), j, T(0), k, T(0.5), s * ld[2], nullptr);
   } else if (q == 1) {
-    sample_adj<T>(A.u, lu, A.Lu, T(i) + T(0.5), T(j) - T(0.5), T(k), s * ld[0], nullptr);
+    sample_adj<T>(A.u, lu, A.Lu, i, T(0.5), j, T(-0.5), k, T(0), s * ld[0], nullptr);
     aadd(&lv[(size_t)i + (size_t)A.Lv.P * ((size_t)j + (size_t)A.Lv.Ly * k)], s * ld[1]);
-    sample_adj<T>(A.w, lw, A.Lw, T(i), T(j) - T(0.5), T(k) + T(0.5), s * ld[2], nullptr);
+    sample_adj<T>(A.w, lw, A.Lw, i, T(0), j, T(-0.5), k, T(0.5), s * ld[2], nullptr);
   } else {
-    sample_adj<T>(A.u, lu, A.Lu, T(i) + T(0.5), T(j), T(k) - T(0.5), s * ld[0], nullptr);
-    sample_adj<T>(A.v, lv, A.Lv, T(i), T(j) + T(0.5), T(k) - T(0.5), s * ld[1], nullptr);
+    sample_adj<T>(A.u, lu, A.Lu, i, T(0.5), j, T(0), k, T(-0.5), s * ld[0], nullptr);
+    sample_adj<T>(A.v, lv, A.Lv, i, T(0), j, T(0.5), k, T(-0.5), s * ld[1], nullptr);
     aadd(&lw[(size_t)i + (size_t)A.Lw.P * ((size_t)j + (size_t)A.Lw.Ly * k)], s * ld[2]);
   }
 }
@@ -595,17 +596,17 @@ __global__ void __launch_bounds__(NT, 2) k_advect_backward_adj(AdvectArgs<T> A, 
   T d[3];
   displacement(A, q, i, j, k, s, d);
   T mn, mx;
-  const T fwd = sample<T, true>(F, L, T(i) - d[0], T(j) - d[1], T(k) - d[2], &mn, &mx);
-  const T bwd = sample<T, false>(Fh, L, T(i) + d[0], T(j) + d[1], T(k) + d[2]);
+  const T fwd = sample<T, true>(F, L, i, -d[0], j, -d[1], k, -d[2], &mn, &mx);
+  const T bwd = sample<T, false>(Fh, L, i, d[0], j, d[1], k, d[2]);
   const T r = fwd + T(0.5) * (F[id] - bwd);
   if (r < mn || r > mx) {
     // clamped: the output is one of the 8 forward-sample values
     const T target = r < mn ? mn : mx;
     int i0, i1, j0, j1, k0, k1;
     T ta, tb, tc;
-    axis_cell(T(i) - d[0], L.Lx, i0, i1, ta);
-    axis_cell(T(j) - d[1], L.Ly, j0, j1, tb);
-    axis_cell(T(k) - d[2], L.Lz, k0, k1, tc);
+    axis_cell(i, -d[0], L.Lx, i0, i1, ta);
+    axis_cell(j, -d[1], L.Ly, j0, j1, tb);
+    axis_cell(k, -d[2], L.Lz, k0, k1, tc);
     const int ii[2] = {i0, i1}, jj[2] = {j0, j1}, kk[2] = {k0, k1};
     for (int cz = 0; cz < 2; ++cz)
       for (int cy = 0; cy < 2; ++cy)
@@ -620,8 +621,8 @@ __global__ void __launch_bounds__(NT, 2) k_advect_backward_adj(AdvectArgs<T> A, 
   }
   aadd(&lF[id], T(0.5) * lam);
   T gf[3], gb[3];
-  sample_adj<T>(F, lF, L, T(i) - d[0], T(j) - d[1], T(k) - d[2], lam, gf);
-  sample_adj<T>(Fh, lFh, L, T(i) + d[0], T(j) + d[1], T(k) + d[2], T(-0.5) * lam, gb);
+  sample_adj<T>(F, lF, L, i, -d[0], j, -d[1], k, -d[2], lam, gf);
+  sample_adj<T>(Fh, lFh, L, i, d[0], j, d[1], k, d[2], T(-0.5) * lam, gb);
   // d(fwd)/dd = -grad f, d(bwd)/dd = +grad fh
   const T ld[3] = {-lam * gf[0] - T(0.5) * lam * gb[0], -lam * gf[1] - T(0.5) * lam * gb[1],
                    -lam * gf[2] - T(0.5) * lam * gb[2]};
@@ -645,7 +646,7 @@ __global__ void __launch_bounds__(NT) k_advect_forward_adj(AdvectArgs<T> A, Adve
   T d[3];
   displacement(A, q, i, j, k, s, d);
   T g[3];
-  sample_adj<T>(F, lF, L, T(i) - d[0], T(j) - d[1], T(k) - d[2], lam, g);
+  sample_adj<T>(F, lF, L, i, -d[0], j, -d[1], k, -d[2], lam, g);
   const T ld[3] = {-lam * g[0], -lam * g[1], -lam * g[2]};
   displacement_adj(A, q, i, j, k, s, ld, J.lu, J.lv, J.lw);
 }

@@ -120,26 +120,46 @@ struct Lattice {
 template <typename T>
 __device__ __forceinline__ T lerp_(T a, T b, T t) { return a + t * (b - a); }
 
+// A lattice coordinate is passed as an integer lattice index plus a small
+// offset (the displacement, or a half-cell shift): the cell then follows
+// from integer arithmetic and the weight t is rounded relative to the
+// offset, not to the index.  Formed as one floating-point number x = base +
+// off, it would be rounded to eps |x| -- 3e-5 of a cell at index 512 in
+// FP32 -- at every backtrace.  Clamped to [0, n - 1] as x would be.
 template <typename T>
-__device__ __forceinline__ void axis_cell(T x, int n, int& i0, int& i1, T& t) {
-  x = fmin(fmax(x, T(0)), T(n - 1));
-  int f = (int)floor(x);
-  f = n >= 2 ? min(f, n - 2) : 0;
+__device__ __forceinline__ void axis_cell(int base, T off, int n, int& i0, int& i1, T& t) {
+  const T fo = floor(off);
+  int f = base + (int)fo;
+  T tt = off - fo;
+  if (f < 0) {                       // below the lattice
+    f = 0;
+    tt = T(0);
+  } else if (f >= n - 1) {           // at or beyond the last point
+    f = n >= 2 ? n - 2 : 0;
+    tt = n >= 2 ? T(1) : T(0);
+  }
   i0 = f;
   i1 = min(f + 1, n - 1);
-  t = x - T(f);
+  t = tt;
+}
+// base + off inside [0, n - 1] (the sample is not clamped along the axis)
+template <typename T>
+__device__ __forceinline__ bool axis_inside(int base, T off, int n) {
+  const T fo = floor(off);
+  const int f = base + (int)fo;
+  return f >= 0 && (f < n - 1 || (f == n - 1 && off == fo));
 }
 
-// Trilinear sample at lattice coordinates (a,b,c), clamped to the lattice;
-// optionally the range of the 8 values used.
+// Trilinear sample at lattice coordinates (ia + oa, ib + ob, ic + oc),
+// clamped to the lattice; optionally the range of the 8 values used.
 template <typename T, bool RANGE>
-__device__ __forceinline__ T sample(const T* __restrict__ F, Lattice L, T a, T b, T c, T* mn = nullptr,
-                                    T* mx = nullptr) {
+__device__ __forceinline__ T sample(const T* __restrict__ F, Lattice L, int ia, T oa, int ib, T ob, int ic, T oc,
+                                    T* mn = nullptr, T* mx = nullptr) {
   int i0, i1, j0, j1, k0, k1;
   T ta, tb, tc;
-  axis_cell(a, L.Lx, i0, i1, ta);
-  axis_cell(b, L.Ly, j0, j1, tb);
-  axis_cell(c, L.Lz, k0, k1, tc);
+  axis_cell(ia, oa, L.Lx, i0, i1, ta);
+  axis_cell(ib, ob, L.Ly, j0, j1, tb);
+  axis_cell(ic, oc, L.Lz, k0, k1, tc);
   const size_t r00 = (size_t)L.P * ((size_t)j0 + (size_t)L.Ly * k0);
   const size_t r10 = (size_t)L.P * ((size_t)j1 + (size_t)L.Ly * k0);
   const size_t r01 = (size_t)L.P * ((size_t)j0 + (size_t)L.Ly * k1);
@@ -178,15 +198,15 @@ template <typename T>
 __device__ __forceinline__ void displacement(const AdvectArgs<T>& A, int q, int i, int j, int k, T s, T d[3]) {
   if (q == 0) {   // u point (i, j+1/2, k+1/2)
     d[0] = s * A.u[(size_t)i + (size_t)A.Lu.P * ((size_t)j + (size_t)A.Lu.Ly * k)];
-    d[1] = s * sample<T, false>(A.v, A.Lv, T(i) - T(0.5), T(j) + T(0.5), T(k));
-    d[2] = s * sample<T, false>(A.w, A.Lw, T(i) - T(0.5), T(j), T(k) + T(0.5));
+    d[1] = s * sample<T, false>(A.v, A.Lv, i, T(-0.5), j, T(0.5), k, T(0));
+    d[2] = s * sample<T, false>(A.w, A.Lw, i, T(-0.5), j, T(0), k, T(0.5));
   } else if (q == 1) {   // v point (i+1/2, j, k+1/2)
-    d[0] = s * sample<T, false>(A.u, A.Lu, T(i) + T(0.5), T(j) - T(0.5), T(k));
+    d[0] = s * sample<T, false>(A.u, A.Lu, i, T(0.5), j, T(-0.5), k, T(0));
     d[1] = s * A.v[(size_t)i + (size_t)A.Lv.P * ((size_t)j + (size_t)A.Lv.Ly * k)];
-    d[2] = s * sample<T, false>(A.w, A.Lw, T(i), T(j) - T(0.5), T(k) + T(0.5));
+    d[2] = s * sample<T, false>(A.w, A.Lw, i, T(0), j, T(-0.5), k, T(0.5));
   } else {   // w point (i+1/2, j+1/2, k)
-    d[0] = s * sample<T, false>(A.u, A.Lu, T(i) + T(0.5), T(j), T(k) - T(0.5));
-    d[1] = s * sample<T, false>(A.v, A.Lv, T(i), T(j) + T(0.5), T(k) - T(0.5));
+    d[0] = s * sample<T, false>(A.u, A.Lu, i, T(0.5), j, T(0), k, T(-0.5));
+    d[1] = s * sample<T, false>(A.v, A.Lv, i, T(0), j, T(0.5), k, T(-0.5));
     d[2] = s * A.w[(size_t)i + (size_t)A.Lw.P * ((size_t)j + (size_t)A.Lw.Ly * k)];
   }
 }
@@ -212,7 +232,7 @@ __device__ __forceinline__ void advect_forward_body(const AdvectArgs<T>& A, cons
   T d[3];
   displacement(A, q, i, j, k, s, d);
   Fh[(size_t)i + (size_t)L.P * ((size_t)j + (size_t)L.Ly * k)] =
-      sample<T, false>(F, L, T(i) - d[0], T(j) - d[1], T(k) - d[2]);
+      sample<T, false>(F, L, i, -d[0], j, -d[1], k, -d[2]);
 }
 
 template <typename T>
@@ -240,8 +260,8 @@ __device__ __forceinline__ void advect_backward_body(const AdvectArgs<T>& A, con
   T d[3];
   displacement(A, q, i, j, k, s, d);
   T mn, mx;
-  const T fwd = sample<T, true>(F, L, T(i) - d[0], T(j) - d[1], T(k) - d[2], &mn, &mx);
-  const T bwd = sample<T, false>(Fh, L, T(i) + d[0], T(j) + d[1], T(k) + d[2]);
+  const T fwd = sample<T, true>(F, L, i, -d[0], j, -d[1], k, -d[2], &mn, &mx);
+  const T bwd = sample<T, false>(Fh, L, i, d[0], j, d[1], k, d[2]);
   const size_t id = (size_t)i + (size_t)L.P * ((size_t)j + (size_t)L.Ly * k);
   T r = fwd + T(0.5) * (F[id] - bwd);
   Ft[id] = fmin(fmax(r, mn), mx);
