@@ -1550,19 +1550,30 @@ class GridImpl final : public uf_grid {
         rec_count += 2;
       };
       auto post = [&](cudaStream_t s) {
-        const dim3 blk(uf::BX, uf::BY);
-        uf::k_pressure_commit<T><<<plane_grid(d.nx, d.ny, d.nz), blk, 0, s>>>(sp, p, pd, gd, st);
-        uf::k_project<T><<<plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1), blk, 0, s>>>(sp, pd, uh, vh, wh);
-        cudaMemcpyAsync(u, uh, P.n_u * sizeof(T), cudaMemcpyDeviceToDevice, s);
-        cudaMemcpyAsync(v, vh, P.n_v * sizeof(T), cudaMemcpyDeviceToDevice, s);
-        cudaMemcpyAsync(w, wh, P.n_w * sizeof(T), cudaMemcpyDeviceToDevice, s);
-        rec_count += 2;
+        uf::k_pressure_commit<T><<<plane_grid(d.nx, d.ny, d.nz), dim3(uf::BX, uf::BY), 0, s>>>(sp, p, pd, gd, st);
+        rec_count++;
       };
       uf_status s = capture(&init_exec, pre, post, &nf, &ns, &ni);
       if (s != UF_OK) return s;
     }
+    uf_status s = ensure_solve_exec();
+    if (s != UF_OK) return s;
     parity = 0;
     UF_CUDA(cudaGraphLaunch(init_exec, stream));
+    s = check_device(nullptr);
+    if (s != UF_OK) return s;
+    // The solve above held the whole initial pressure in its grid-precision
+    // iterate, which bounds its true residual by about eps ||A|| ||p||.  One
+    // more solve from the committed pressure (initial residual formed on the
+    // pressure store) removes that remainder; then the projection.
+    UF_CUDA(copy_cell_ps(gd, pd));
+    UF_CUDA(cudaGraphLaunch(solve_exec, stream));
+    uf::k_project<T><<<plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1), dim3(uf::BX, uf::BY), 0, stream>>>(sp, pd, uh, vh,
+                                                                                                       wh);
+    UF_CUDA(cudaGetLastError());
+    UF_CUDA(cudaMemcpyAsync(u, uh, P.n_u * sizeof(T), cudaMemcpyDeviceToDevice, stream));
+    UF_CUDA(cudaMemcpyAsync(v, vh, P.n_v * sizeof(T), cudaMemcpyDeviceToDevice, stream));
+    UF_CUDA(cudaMemcpyAsync(w, wh, P.n_w * sizeof(T), cudaMemcpyDeviceToDevice, stream));
     UF_CUDA(copy_cell_ps(gd, pd));   // no previous pressure: the first guess is p itself
     have_state = true;
     return check_device(nullptr);
@@ -1744,24 +1755,29 @@ class GridImpl final : public uf_grid {
     return copy_out(y, d0, d.nx, d.ny, d.nz, P.Pc);
   }
 
+  // Stand-alone solve of A p = b (b in the grid's b buffer) from the guess
+  // in the pressure store, committed into it.
+  uf_status ensure_solve_exec() {
+    if (solve_exec) return UF_OK;
+    int nf, ns, ni;
+    auto pre = [&](cudaStream_t s2) {
+      int zc;
+      dim3 g = chunk_grid(d.nx, d.ny, d.nz, &zc);
+      uf::k_solve_reset<T><<<g, dim3(uf::BX, uf::BY), 0, s2>>>(lv[0], b, zc, partials, st);
+      rec_count++;
+    };
+    auto post = [&](cudaStream_t s2) {
+      uf::k_pressure_commit<T><<<plane_grid(d.nx, d.ny, d.nz), dim3(uf::BX, uf::BY), 0, s2>>>(sp, p, pd, gd, st);
+      rec_count++;
+    };
+    return capture(&solve_exec, pre, post, &nf, &ns, &ni);
+  }
+
   uf_status poisson_solve(const void* bsrc, int* iters, double* rel) override {
     uf_status s = copy_in(b, d.nx, d.ny, d.nz, P.Pc, bsrc);
     if (s != UF_OK) return s;
-    if (!solve_exec) {
-      int nf, ns, ni;
-      auto pre = [&](cudaStream_t s2) {
-        int zc;
-        dim3 g = chunk_grid(d.nx, d.ny, d.nz, &zc);
-        uf::k_solve_reset<T><<<g, dim3(uf::BX, uf::BY), 0, s2>>>(lv[0], b, zc, partials, st);
-        rec_count++;
-      };
-      auto post = [&](cudaStream_t s2) {
-        uf::k_pressure_commit<T><<<plane_grid(d.nx, d.ny, d.nz), dim3(uf::BX, uf::BY), 0, s2>>>(sp, p, pd, gd, st);
-        rec_count++;
-      };
-      s = capture(&solve_exec, pre, post, &nf, &ns, &ni);
-      if (s != UF_OK) return s;
-    }
+    s = ensure_solve_exec();
+    if (s != UF_OK) return s;
     UF_CUDA(cudaGraphLaunch(solve_exec, stream));
     UF_CUDA(copy_cell_ps(gd, pd));
     uf_step_stats o;
