@@ -125,19 +125,31 @@ struct SmoothW {
   T w1, w2;   // post-smoothing passes
 };
 
+// Reciprocal of a diagonal entry for the smoothers.  FP32: the hardware
+// approximation rcp.approx.ftz (at most 1 ulp off), one instruction where an
+// IEEE division is a subroutine; the smoother only needs a fixed diagonal
+// scaling, and the same scaling in every sweep keeps the V-cycle symmetric.
+// FP64: exact.
+__device__ __forceinline__ float rdiag(float D) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(D));
+  return r;
+}
+__device__ __forceinline__ double rdiag(double D) { return 1.0 / D; }
+
 // Pre-smoothing from zero with q = r/D staged: weighted Jacobi x2 = pa q_c +
 // pb/D_c sum w_a q_nb;  RBGS red q_c, black q_c + sum w_a q_nb / D_c.
 template <int SM, typename T>
 __device__ __forceinline__ T presmooth(T qc, T s, T D, const SmoothW<T>& W, bool red) {
-  if (SM == SM_JACOBI) return W.pa * qc + W.pb * s / D;
-  return red ? qc : qc + s / D;
+  if (SM == SM_JACOBI) return W.pa * qc + W.pb * s * rdiag(D);
+  return red ? qc : qc + s * rdiag(D);
 }
 // Post-smoothing pass on t: weighted Jacobi t + w (r - D t + s)/D; RBGS
 // relaxes the colour `relax` and keeps the other.
 template <int SM, typename T>
 __device__ __forceinline__ T relax(T tc, T rc, T s, T D, T omega, bool active) {
-  if (SM == SM_JACOBI) return tc + omega * (rc - D * tc + s) / D;
-  return active ? (rc + s) / D : tc;
+  if (SM == SM_JACOBI) return tc + omega * (rc - D * tc + s) * rdiag(D);
+  return active ? (rc + s) * rdiag(D) : tc;
 }
 
 // ------------------------------------------------------------ down -------
@@ -226,11 +238,11 @@ __device__ __forceinline__ void mg_down_body(const Level<T>& F, const Level<T>& 
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       if (h == 1 && !mq.has1) break;
-      dst[sq[h]] = (kin && pq[h].ok) ? (CG ? pr[h] - alpha * pqv[h] : pr[h]) / (pq[h].dxy + dz) : T(0);
+      dst[sq[h]] = (kin && pq[h].ok) ? (CG ? pr[h] - alpha * pqv[h] : pr[h]) * rdiag(pq[h].dxy + dz) : T(0);
     }
   };
-  auto computeX = [&](int k) {
-    T* dst = sX[ring3(k)];
+  auto computeX = [&](int k, int slot) {
+    T* dst = sX[slot];
     const T* qm = sQ[ring4(k - 1)];
     const T* qc = sQ[ring4(k)];
     const T* qp = sQ[ring4(k + 1)];
@@ -257,12 +269,14 @@ __device__ __forceinline__ void mg_down_body(const Level<T>& F, const Level<T>& 
   issueQ(k0 - 1); commitQ(k0 - 1);
   issueQ(k0); commitQ(k0);
   issueQ(k0 + 1);
+  // ring slots of the pre-smoothed planes k - 1, k, k + 1, rotated once per plane
+  int xs_m = ring3(k0 - 1), xs_c = ring3(k0), xs_p = ring3(k0 + 1);
   __syncthreads();
-  computeX(k0 - 1);
+  computeX(k0 - 1, xs_m);
   commitQ(k0 + 1);
   issueQ(k0 + 2);
   __syncthreads();
-  computeX(k0);
+  computeX(k0, xs_c);
   __syncthreads();
   // a z-coarsened level of odd extent ends on a pair whose second plane is
   // outside the domain (its residual is zero)
@@ -283,13 +297,13 @@ __device__ __forceinline__ void mg_down_body(const Level<T>& F, const Level<T>& 
     commitQ(k + 2);
     issueQ(k + 3);
     __syncthreads();
-    computeX(k + 1);
+    computeX(k + 1, xs_p);
     __syncthreads();
     T res = 0;
     if (own) {
-      const T* xm = sX[ring3(k - 1)];
-      const T* xc = sX[ring3(k)];
-      const T* xp = sX[ring3(k + 1)];
+      const T* xm = sX[xs_m];
+      const T* xc = sX[xs_c];
+      const T* xp = sX[xs_p];
       const T xv = xc[b1];
       F.x[oc] = xv;
       res = (po.dxy + diag_z(F, k)) * (sQ[ring4(k)][b2] - xv) + F.wx * (xc[b1 - 1] + xc[b1 + 1]) +
@@ -317,6 +331,10 @@ __device__ __forceinline__ void mg_down_body(const Level<T>& F, const Level<T>& 
         C.r[lidx(C, ci, cj, kc)] = sum;
       }
     }
+    const int xs_t = xs_m;
+    xs_m = xs_c;
+    xs_c = xs_p;
+    xs_p = xs_t;
   }
   if (CG) {
     acc += dacc.value();
@@ -425,8 +443,8 @@ __device__ __forceinline__ void mg_up_body(const Level<T>& F, const Level<T>& C,
 #pragma unroll
     for (int h = 0; h < 2; ++h) pr[h] = (kin && pu[h].ok) ? rcur[(size_t)k * PS + pu[h].off] : T(0);
   };
-  auto computeU = [&](int k) {
-    T* dst = sU[ring3(k)];
+  auto computeU = [&](int k, int slot) {
+    T* dst = sU[slot];
     const T* tm = sT[ring4(k - 1)];
     const T* tc = sT[ring4(k)];
     const T* tp = sT[ring4(k + 1)];
@@ -451,13 +469,15 @@ __device__ __forceinline__ void mg_up_body(const Level<T>& F, const Level<T>& C,
   issueT(k0); commitT(k0);
   issueT(k0 + 1);
   issueR(k0 - 1);
+  // ring slots of the relaxed planes k - 1, k, k + 1, rotated once per plane
+  int us_m = ring3(k0 - 1), us_c = ring3(k0), us_p = ring3(k0 + 1);
   __syncthreads();
-  computeU(k0 - 1);
+  computeU(k0 - 1, us_m);
   commitT(k0 + 1);
   issueT(k0 + 2);
   issueR(k0);
   __syncthreads();
-  computeU(k0);
+  computeU(k0, us_c);
   issueR(k0 + 1);
   __syncthreads();
   const int b = (tx + 1) + XX * (ty + 1);
@@ -468,18 +488,22 @@ __device__ __forceinline__ void mg_up_body(const Level<T>& F, const Level<T>& C,
     commitT(k + 2);
     issueT(k + 3);
     __syncthreads();
-    computeU(k + 1);
+    computeU(k + 1, us_p);
     issueR(k + 2);
     __syncthreads();
     if (po.ok) {
-      const T* um = sU[ring3(k - 1)];
-      const T* uc = sU[ring3(k)];
-      const T* up = sU[ring3(k + 1)];
+      const T* um = sU[us_m];
+      const T* uc = sU[us_c];
+      const T* up = sU[us_p];
       const T s = F.wx * (uc[b - 1] + uc[b + 1]) + F.wy * (uc[b - XX] + uc[b + XX]) + F.wz * (um[b] + up[b]);
       const T zv = relax<SM>(uc[b], o_r, s, po.dxy + diag_z(F, k), W.w2, ((opar + k) & 1) == 0);
       out[oc] = zv;
       if (FINEST) dacc.add(o_r, zv);
     }
+    const int us_t = us_m;
+    us_m = us_c;
+    us_c = us_p;
+    us_p = us_t;
   }
   if (FINEST) {
     acc += dacc.value();
@@ -569,7 +593,7 @@ __device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, const SmoothW
     for (int e = tid; e < n; e += TAIL_T) {
       const int i = e % L.nx, j = (e / L.nx) % L.ny, k = e / (L.nx * L.ny);
       const int b = (i + 1) + X * (j + 1) + P * (k + 1);
-      u[b] = r[b] / diag_of(L, i, j, k);
+      u[b] = r[b] * rdiag(diag_of(L, i, j, k));
     }
     __syncthreads();
     for (int e = tid; e < n; e += TAIL_T) {
