@@ -600,6 +600,36 @@ def run_large(args):
     return 0
 
 
+# --------------------------------------------------------- vortex shedding
+
+def run_karman(args):
+    """The supplement's solver validation: flow past a 0.046 m cylinder on
+    512 x 768 cells of 2 mm, inflow 2-20 m/s; the shedding frequency from a
+    wake probe against St = 0.198 (1 - 19.7/Re).  Each speed runs at the
+    supplement's fixed dt = 1e-4 s and at the dt of cell Courant number 1."""
+    import torch
+    from paper_2204_01117_gb300 import uf, validation
+    torch.cuda.set_device(0)
+    uf.build()
+    uf.load()
+    rows = []
+    t0 = time.perf_counter()
+    for U in (2.0, 5.0, 10.0, 20.0):
+        for mode, kw in (("dt=1e-4 s", dict()), ("Courant 1", dict(cfl=1.0))):
+            r = validation.shedding_run(U, **kw)
+            r["mode"] = mode
+            r["St_error"] = r["St"] / r["St_formula"] - 1.0
+            rows.append(r)
+    line = {"metric": "Strouhal number of the vortex street vs St = 0.198 (1 - 19.7/Re)",
+            "unit": "relative error", "impl": "ours", "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "cylinder D = 0.046 m, 512 x 768 x 1 cells of 2 mm, inflow 2-20 m/s through y-, "
+                                   "outflow y+, slip x sides and z; probe 3 D downstream on the axis",
+                       "seconds": time.perf_counter() - t0},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- oracle arm
 
 def oracle_sample(max_seconds: float = 150.0, steps_wanted: int = 1):
@@ -770,9 +800,13 @@ def main():
     ap.add_argument("--large", action="store_true",
                     help="print the plain-FP64 vs FP32 comparison on the 512x512x128 block instead of the bench line")
     ap.add_argument("--large-grid", default="512x512x128", help="grid of --large (NXxNYxNZ)")
+    ap.add_argument("--karman", action="store_true",
+                    help="print the vortex-shedding validation table instead of the bench line")
     args = ap.parse_args()
     if args.large:
         return run_large(args)
+    if args.karman:
+        return run_karman(args)
     if args.steps is None:
         args.steps = 50
     if args.preconditioners:

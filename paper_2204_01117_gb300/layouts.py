@@ -253,6 +253,41 @@ def design_lattice(nx=128, ny=128, nz=48, h=2.0, cols=4, rows=3, footprint=20.0,
                           ckpt_every=ckpt_every, regions=np.array(regions).reshape(-1, 6))
 
 
+@dataclass
+class CylinderScenario(Scenario):
+    """Flow past a circular cylinder in a quasi-2D channel (one cell in z,
+    slip in z), for the vortex-shedding validation."""
+    D: float = 0.046                    # cylinder diameter [m]
+    centre: tuple = (0.512, 0.3)        # cylinder axis (x, y) [m]
+    fixed_dt: float = 1e-4              # [s]
+    I: float = 1e-3                     # inlet turbulence intensity
+    L: float = 0.046                    # inlet turbulence length scale [m]
+
+    def params(self) -> dict:
+        d = super().params()
+        d.update(fixed_dt=self.fixed_dt, I=self.I, L=self.L)
+        return d
+
+
+def karman_cylinder(U: float, nx=512, ny=768, h=2e-3, D=0.046, centre_y=0.3, dt=1e-4, I=1e-3,
+                    L=None) -> CylinderScenario:
+    """The vortex-street benchmark of the supplement's solver validation:
+    512 x 768 cells of 2 mm, a cylinder of 0.046 m diameter, inflow U through
+    the y- side (wind direction +y), outflow through y+, slip walls on the x
+    sides, dt = 1e-4 s (or the dt given).  The cylinder is solid (phi = 0) in
+    every cell whose centre lies inside it, open elsewhere; it sits on the
+    channel axis, centre_y from the inlet.  The inlet turbulence is nearly
+    laminar (I = 1e-3, length scale D): the supplement states none."""
+    xc, yc = nx * h / 2, centre_y
+    x = (np.arange(nx) + 0.5) * h
+    y = (np.arange(ny) + 0.5) * h
+    X, Y = np.meshgrid(x, y)
+    phi = ((X - xc) ** 2 + (Y - yc) ** 2 > (D / 2) ** 2).astype(np.float64)[None]
+    return CylinderScenario(nx, ny, 1, h, phi, wind_dir_deg=90.0, u_ref=U, inflow_loglaw=False,
+                            ground_noslip=False, name=f"karman_{nx}x{ny}_U{U:g}", D=D, centre=(xc, yc),
+                            fixed_dt=dt, I=I, L=D if L is None else L)
+
+
 def empty_domain(nx, ny, nz, h=1.0, u_ref=2.0, wind_dir_deg=0.0, ground_noslip=False,
                  loglaw=False) -> Scenario:
     phi = np.ones((nz, ny, nx))
