@@ -304,6 +304,28 @@ uf_status uf_adjoint_run_ex(uf_grid* g, void* d_ws, size_t bytes, int nsteps, in
 uf_status uf_step_vjp(uf_grid* g, void* d_ws, size_t bytes, const void* const* lam_out, void* const* lam_in,
                       void* lam_phi);
 
+/* ---- Sub-steps and their transposes (test support) --------------------
+ * One sub-step of uf_step applied in isolation to dense inputs (grid
+ * precision, host or device, in the order listed), or, with transpose = 1,
+ * its hand-written transpose at those inputs: out = J^T cot, the adjoints of
+ * the inputs from cotangents `cot` of the outputs.  Face fields are u
+ * (nx+1, ny, nz), v (nx, ny+1, nz), w (nx, ny, nz+1); cell fields (nx, ny,
+ * nz); x fastest.
+ *   UF_SUB_EDDY     (a1)  in u, v, w, k, omega  -> nu_t
+ *   UF_SUB_ADVECT   (a2)  in u, v, w            -> u~, v~, w~ (interior faces; others 0)
+ *   UF_SUB_DIFFUSE  (a3)  in u~, v~, w~, nu_t   -> u2, v2, w2 (interior faces; others 0)
+ *   UF_SUB_DRAG_BC  (a4, a5) in u2, v2, w2, phi -> u3, v3, w3 (every face)
+ *   UF_SUB_PROJECT  (a6-a8) in u3, v3, w3       -> u1, v1, w1 (pressure solved from 0)
+ *   UF_SUB_TURB     (a9)  in u1, v1, w1, k, omega -> k', omega'
+ * The grid needs fixed_dt > 0.  The call allocates and frees a scratch
+ * block, synchronises, and leaves the grid without a usable state (set one
+ * before stepping).  Errors: UF_ERR_ARG (no fixed dt, unknown sub-step, a
+ * NULL list or buffer), UF_ERR_CUDA. */
+enum { UF_SUB_EDDY = 0, UF_SUB_ADVECT = 1, UF_SUB_DIFFUSE = 2, UF_SUB_DRAG_BC = 3, UF_SUB_PROJECT = 4,
+       UF_SUB_TURB = 5 };
+uf_status uf_substep(uf_grid* g, int which, int transpose, const void* const* in, const void* const* cot,
+                     void* const* out);
+
 /* Parametric design -> porosity (smoothed cut-cell idea of Sec. 3, "Urban
  * model resolving"): nbox (<= 64) boxes with base footprints
  * boxes[4i..4i+3] = (x_a, x_b, y_a, y_b) [m] and parameters

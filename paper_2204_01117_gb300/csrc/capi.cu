@@ -1627,6 +1627,174 @@ class GridImpl final : public uf_grid {
     return UF_OK;
   }
 
+  // ------------------------------------------------------ sub-steps ------
+  // One sub-step of the step, or its transpose, on dense inputs (test
+  // support, uf_substep).  Works in a scratch block of four face sets and
+  // eight cell arrays allocated for the call; the projection also uses the
+  // solver's arrays and the pressure store, so the grid's state is not
+  // kept.
+  uf_status substep(int which, int tr, const void* const* in, const void* const* cot, void* const* out) override {
+    if (!(d.fixed_dt > 0)) return fail(UF_ERR_ARG, "sub-steps need a fixed time step (fixed_dt > 0)");
+    if (!in || !out || (tr && !cot)) return fail(UF_ERR_ARG, "NULL buffer list");
+    if (which < UF_SUB_EDDY || which > UF_SUB_TURB) return fail(UF_ERR_ARG, "unknown sub-step");
+    const size_t fN = face_set(), cN = a64(P.n_c);
+    T* blk = nullptr;
+    UF_CUDA(cudaMalloc(&blk, (4 * fN + 8 * cN) * sizeof(T)));
+    uf_status s = substep_in(which, tr, in, cot, out, blk, fN, cN);
+    cudaError_t e = cudaStreamSynchronize(stream);
+    cudaFree(blk);
+    if (s != UF_OK) return s;
+    UF_CUDA(e);
+    return check_device(nullptr);
+  }
+  uf_status substep_in(int which, int tr, const void* const* in, const void* const* cot, void* const* out, T* blk,
+                       size_t fN, size_t cN) {
+    FaceSet S[4];
+    T* C[8];
+    for (int a = 0; a < 4; ++a) S[a] = faces_at(blk + a * fN);
+    for (int a = 0; a < 8; ++a) C[a] = blk + 4 * fN + a * cN;
+    UF_CUDA(cudaMemsetAsync(blk, 0, (4 * fN + 8 * cN) * sizeof(T), stream));
+    auto faces_in = [&](FaceSet f, const void* const* src) -> uf_status {
+      uf_status r = copy_in(f.u, d.nx + 1, d.ny, d.nz, P.Pu, src[0]);
+      if (r == UF_OK) r = copy_in(f.v, d.nx, d.ny + 1, d.nz, P.Pc, src[1]);
+      if (r == UF_OK) r = copy_in(f.w, d.nx, d.ny, d.nz + 1, P.Pc, src[2]);
+      return r;
+    };
+    auto faces_out = [&](void* const* dst, FaceSet f) -> uf_status {
+      uf_status r = copy_out(dst[0], f.u, d.nx + 1, d.ny, d.nz, P.Pu);
+      if (r == UF_OK) r = copy_out(dst[1], f.v, d.nx, d.ny + 1, d.nz, P.Pc);
+      if (r == UF_OK) r = copy_out(dst[2], f.w, d.nx, d.ny, d.nz + 1, P.Pc);
+      return r;
+    };
+    auto cell_in = [&](T* c, const void* src) { return copy_in(c, d.nx, d.ny, d.nz, P.Pc, src); };
+    auto cell_out = [&](void* dst, const T* c) { return copy_out(dst, c, d.nx, d.ny, d.nz, P.Pc); };
+    const dim3 bk(uf::BX, uf::BY);
+    const dim3 gc = plane_grid(d.nx, d.ny, d.nz);
+    const dim3 ga = plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1);
+    uf_status s = UF_OK;
+#define UF_TRY(x) do { s = (x); if (s != UF_OK) return s; } while (0)
+    switch (which) {
+      case UF_SUB_EDDY: {       // in u, v, w, k, omega -> nu_t
+        UF_TRY(faces_in(S[0], in));
+        UF_TRY(cell_in(C[0], in[3]));
+        UF_TRY(cell_in(C[1], in[4]));
+        if (!tr) {
+          uf::k_eddy_viscosity<T><<<gc, bk, 0, stream>>>(sp, S[0].u, S[0].v, S[0].w, C[0], C[1], C[2]);
+          UF_CUDA(cudaGetLastError());
+          return cell_out(out[0], C[2]);
+        }
+        UF_TRY(cell_in(C[2], cot[0]));
+        uf::k_eddy_viscosity_adj<T><<<gc, bk, 0, stream>>>(sp, S[0].u, S[0].v, S[0].w, C[0], C[1], C[2], C[3], C[4],
+                                                            S[1].u, S[1].v, S[1].w);
+        UF_CUDA(cudaGetLastError());
+        UF_TRY(faces_out(out, S[1]));
+        UF_TRY(cell_out(out[3], C[3]));
+        return cell_out(out[4], C[4]);
+      }
+      case UF_SUB_ADVECT: {     // in u, v, w -> MacCormack result on interior faces
+        UF_TRY(faces_in(S[0], in));
+        uf::AdvectArgs<T> Aa = advect_args();
+        Aa.u = S[0].u; Aa.v = S[0].v; Aa.w = S[0].w;
+        Aa.uh = S[1].u; Aa.vh = S[1].v; Aa.wh = S[1].w;
+        Aa.ut = S[2].u; Aa.vt = S[2].v; Aa.wt = S[2].w;
+        uf::k_advect_forward<T><<<ga, bk, 0, stream>>>(Aa);
+        uf::k_advect_backward<T><<<ga, bk, 0, stream>>>(Aa);
+        UF_CUDA(cudaGetLastError());
+        if (!tr) return faces_out(out, S[2]);
+        UF_TRY(faces_in(S[2], cot));
+        uf::AdvectAdj<T> Ja{S[2].u, S[2].v, S[2].w, S[3].u, S[3].v, S[3].w, nullptr, nullptr, nullptr};
+        FaceSet L = faces_at(C[0]);   // C[0..] hold a face set: 3 face arrays fit in 8 cell arrays
+        UF_CUDA(cudaMemsetAsync(C[0], 0, fN * sizeof(T), stream));
+        Ja.lu = L.u; Ja.lv = L.v; Ja.lw = L.w;
+        uf::k_advect_backward_adj<T><<<ga, bk, 0, stream>>>(Aa, Ja);
+        uf::k_advect_forward_adj<T><<<ga, bk, 0, stream>>>(Aa, Ja);
+        UF_CUDA(cudaGetLastError());
+        return faces_out(out, L);
+      }
+      case UF_SUB_DIFFUSE: {    // in u~, v~, w~, nu_t -> u2 (interior faces)
+        UF_TRY(faces_in(S[0], in));
+        UF_TRY(cell_in(C[0], in[3]));
+        if (!tr) {
+          uf::k_diffuse<T><<<ga, bk, 0, stream>>>(sp, S[0].u, S[0].v, S[0].w, C[0], S[1].u, S[1].v, S[1].w);
+          UF_CUDA(cudaGetLastError());
+          return faces_out(out, S[1]);
+        }
+        UF_TRY(faces_in(S[2], cot));
+        uf::k_diffuse_adj<T><<<ga, bk, 0, stream>>>(sp, S[0].u, S[0].v, S[0].w, C[0], S[2].u, S[2].v, S[2].w, S[3].u,
+                                                     S[3].v, S[3].w, C[1]);
+        UF_CUDA(cudaGetLastError());
+        UF_TRY(faces_out(out, S[3]));
+        return cell_out(out[3], C[1]);
+      }
+      case UF_SUB_DRAG_BC: {    // in u2, v2, w2, phi -> u3 (every face)
+        UF_TRY(faces_in(S[0], in));
+        UF_TRY(cell_in(C[0], in[3]));
+        uf::k_drag_coeff<T><<<(unsigned)((P.n_c + 255) / 256), 256, 0, stream>>>(C[0], C[1], P.n_c, d.Cd, d.a, d.b,
+                                                                                  d.e);
+        if (!tr) {
+          uf::k_drag_bc<T><<<ga, bk, 0, stream>>>(sp, S[0].u, S[0].v, S[0].w, C[1], S[1].u, S[1].v, S[1].w);
+          UF_CUDA(cudaGetLastError());
+          return faces_out(out, S[1]);
+        }
+        UF_TRY(faces_in(S[2], cot));
+        uf::k_drag_bc_adj<T><<<ga, bk, 0, stream>>>(sp, S[0].u, S[0].v, S[0].w, C[1], S[2].u, S[2].v, S[2].w, S[3].u,
+                                                     S[3].v, S[3].w, C[2]);
+        uf::k_dphi<T><<<(unsigned)((P.n_c + 255) / 256), 256, 0, stream>>>(C[0], C[2], C[3], P.n_c, d.Cd, d.a, d.b,
+                                                                            d.e);
+        UF_CUDA(cudaGetLastError());
+        UF_TRY(faces_out(out, S[3]));
+        return cell_out(out[3], C[3]);
+      }
+      case UF_SUB_PROJECT: {    // in u3, v3, w3 -> projected u1 (pressure solved from zero)
+        UF_TRY(faces_in(S[0], in));
+        if (!tr) {
+          int zc;
+          const dim3 gr = chunk_grid(d.nx, d.ny, d.nz, &zc);
+          UF_CUDA(cudaMemsetAsync(pd, 0, P.n_c * sizeof(uf::PStore<T>), stream));
+          UF_CUDA(cudaMemsetAsync(gd, 0, P.n_c * sizeof(uf::PStore<T>), stream));
+          uf::k_pressure_rhs<T><<<gr, bk, 0, stream>>>(sp, S[0].u, S[0].v, S[0].w, b, zc, partials, st);
+          UF_CUDA(cudaGetLastError());
+          UF_TRY(ensure_solve_exec());
+          UF_CUDA(cudaGraphLaunch(solve_exec, stream));
+          uf::k_project<T><<<ga, bk, 0, stream>>>(sp, pd, S[0].u, S[0].v, S[0].w);
+          UF_CUDA(cudaGetLastError());
+          return faces_out(out, S[0]);
+        }
+        UF_TRY(faces_in(S[1], cot));
+        T* mu = C[0];
+        T* badj = C[1];
+        UF_TRY(ensure_adj_solve(mu, badj));
+        uf::k_proj_adj_rhs<T><<<gc, bk, 0, stream>>>(sp, S[1].u, S[1].v, S[1].w, badj, mu, C[2]);
+        UF_CUDA(cudaGetLastError());
+        UF_CUDA(cudaGraphLaunch(adj_solve_exec, stream));
+        uf::k_proj_adj_apply<T><<<ga, bk, 0, stream>>>(sp, mu, S[1].u, S[1].v, S[1].w);
+        UF_CUDA(cudaGetLastError());
+        return faces_out(out, S[1]);
+      }
+      case UF_SUB_TURB: {       // in u1, v1, w1, k, omega -> k', omega'
+        UF_TRY(faces_in(S[0], in));
+        UF_TRY(cell_in(C[0], in[3]));
+        UF_TRY(cell_in(C[1], in[4]));
+        if (!tr) {
+          uf::k_turbulence<T><<<gc, bk, 0, stream>>>(sp, S[0].u, S[0].v, S[0].w, C[0], C[1], C[2], C[3]);
+          UF_CUDA(cudaGetLastError());
+          UF_TRY(cell_out(out[0], C[2]));
+          return cell_out(out[1], C[3]);
+        }
+        UF_TRY(cell_in(C[4], cot[0]));
+        UF_TRY(cell_in(C[5], cot[1]));
+        uf::k_turbulence_adj<T><<<gc, bk, 0, stream>>>(sp, S[0].u, S[0].v, S[0].w, C[0], C[1], C[4], C[5], C[6], C[7],
+                                                        S[1].u, S[1].v, S[1].w);
+        UF_CUDA(cudaGetLastError());
+        UF_TRY(faces_out(out, S[1]));
+        UF_TRY(cell_out(out[3], C[6]));
+        return cell_out(out[4], C[7]);
+      }
+    }
+#undef UF_TRY
+    return fail(UF_ERR_ARG, "unknown sub-step");
+  }
+
   // ------------------------------------------------------------- objectives
   // Cell index range whose centres lie in [a, b] (m) along an axis of n cells.
   void centre_range(double a, double b, int n, int* lo, int* hi) const {
@@ -1916,6 +2084,11 @@ uf_status uf_adjoint_run_ex(uf_grid* g, void* d_ws, size_t bytes, int nsteps, in
                             const uf_objective_desc* obj, void* dJ_dphi, double* J_out) {
   UF_NEED(g);
   return g->adjoint_run_ex(d_ws, bytes, nsteps, ckpt_every, obj, dJ_dphi, J_out);
+}
+uf_status uf_substep(uf_grid* g, int which, int transpose, const void* const* in, const void* const* cot,
+                     void* const* out) {
+  UF_NEED(g);
+  return g->substep(which, transpose, in, cot, out);
 }
 uf_status uf_step_vjp(uf_grid* g, void* d_ws, size_t bytes, const void* const* lam_out, void* const* lam_in,
                       void* lam_phi) {

@@ -62,6 +62,15 @@ class StepStats(ctypes.Structure):
 
 
 MAX_LEVELS = 16
+# uf_substep: id, input fields, output fields (include/uf.h, "Sub-steps")
+SUBSTEPS = {
+    "eddy": (0, ("u", "v", "w", "k", "omega"), ("nut",)),
+    "advect": (1, ("u", "v", "w"), ("u", "v", "w")),
+    "diffuse": (2, ("u", "v", "w", "nut"), ("u", "v", "w")),
+    "drag_bc": (3, ("u", "v", "w", "phi"), ("u", "v", "w")),
+    "project": (4, ("u", "v", "w"), ("u", "v", "w")),
+    "turb": (5, ("u", "v", "w", "k", "omega"), ("k", "omega")),
+}
 MAX_REGIONS = 8
 
 
@@ -197,6 +206,8 @@ def load():
     lib.uf_adjoint_run_ex.argtypes = [vp, vp, ctypes.c_size_t, ip, ip, P(ObjectiveDesc), vp, P(dp)]
     lib.uf_adjoint_run_ex.restype = ip
     lib.uf_step_vjp.argtypes = [vp, vp, ctypes.c_size_t, P(vp), P(vp), vp]
+    lib.uf_substep.argtypes = [vp, ip, ip, P(vp), P(vp), P(vp)]
+    lib.uf_substep.restype = ip
     lib.uf_step_vjp.restype = ip
     lib.uf_design_to_phi.argtypes = [vp, ip, P(dp), P(dp), dp, vp]
     lib.uf_design_to_phi.restype = ip
@@ -424,6 +435,29 @@ class Grid:
         J = ctypes.c_double()
         check(self.lib.uf_objective(self._h, z_lo, z_hi, u_hi, u_lo, ctypes.byref(J)))
         return J.value
+
+    def substep(self, name: str, inputs, cot=None):
+        """One sub-step (uf_substep) on the given inputs (list of arrays in the
+        order of SUBSTEPS[name]); with `cot` (cotangents of the outputs) its
+        transpose instead.  Returns the outputs (or the input adjoints) as
+        numpy arrays.  Test support: the grid's state is not kept."""
+        which, ins, outs = SUBSTEPS[name]
+        keep = [np.ascontiguousarray(a, dtype=self.np_dtype) for a in inputs]
+        assert len(keep) == len(ins) and all(a.shape == self.shapes[n] for a, n in zip(keep, ins))
+        vp = ctypes.c_void_p
+        inp = (vp * len(keep))(*[a.ctypes.data for a in keep])
+        if cot is None:
+            res = [np.empty(self.shapes[n], dtype=self.np_dtype) for n in outs]
+            cp = None
+        else:
+            ck = [np.ascontiguousarray(a, dtype=self.np_dtype) for a in cot]
+            assert len(ck) == len(outs) and all(a.shape == self.shapes[n] for a, n in zip(ck, outs))
+            keep += ck
+            cp = (vp * len(ck))(*[a.ctypes.data for a in ck])
+            res = [np.empty(self.shapes[n], dtype=self.np_dtype) for n in ins]
+        outp = (vp * len(res))(*[a.ctypes.data for a in res])
+        check(self.lib.uf_substep(self._h, which, 0 if cot is None else 1, inp, cp, outp))
+        return res
 
     def objective_ex(self, objective) -> float:
         """Any objective of uf_objective_ex (see objective_desc)."""
