@@ -288,6 +288,88 @@ def karman_cylinder(U: float, nx=512, ny=768, h=2e-3, D=0.046, centre_y=0.3, dt=
                             fixed_dt=dt, I=I, L=D if L is None else L)
 
 
+# ------------------------------------------------------------ meshes ----
+# Closed triangle meshes (n, 3, 3) [m] for the mesh resolver; every
+# triangle wound counter-clockwise seen from outside.
+
+def box_mesh(x0, x1, y0, y1, z0, z1) -> np.ndarray:
+    """The 12 triangles of an axis-aligned box."""
+    c = np.array([[x0, y0, z0], [x1, y0, z0], [x1, y1, z0], [x0, y1, z0],
+                  [x0, y0, z1], [x1, y0, z1], [x1, y1, z1], [x0, y1, z1]], dtype=np.float64)
+    quads = [(0, 3, 2, 1), (4, 5, 6, 7), (0, 1, 5, 4), (1, 2, 6, 5), (2, 3, 7, 6), (3, 0, 4, 7)]
+    return np.array([[c[a], c[b], c[d]] for a, b, cc, d in quads for (b, d) in ((b, cc), (cc, d))])
+
+
+def prism_mesh(cx, cy, radius, sides, angle, z0, z1) -> np.ndarray:
+    """A building: the convex regular polygon of `sides` corners (first at
+    `angle`) around (cx, cy) extruded from z0 to z1."""
+    t = angle + 2 * np.pi * np.arange(sides) / sides
+    ring = np.stack([cx + radius * np.cos(t), cy + radius * np.sin(t)], axis=1)
+    tris = []
+    for a in range(sides):
+        b = (a + 1) % sides
+        p0, p1 = ring[a], ring[b]
+        tris.append([[cx, cy, z0], [p1[0], p1[1], z0], [p0[0], p0[1], z0]])     # floor
+        tris.append([[cx, cy, z1], [p0[0], p0[1], z1], [p1[0], p1[1], z1]])     # roof
+        tris.append([[p0[0], p0[1], z0], [p1[0], p1[1], z0], [p1[0], p1[1], z1]])
+        tris.append([[p0[0], p0[1], z0], [p1[0], p1[1], z1], [p0[0], p0[1], z1]])
+    return np.array(tris, dtype=np.float64)
+
+
+def icosphere_mesh(cx, cy, cz, r, levels=1, scale=(1.0, 1.0, 1.0)) -> np.ndarray:
+    """A canopy: the icosahedron subdivided `levels` times, projected onto
+    the sphere of radius r and stretched by `scale` per axis."""
+    g = (1 + 5 ** 0.5) / 2
+    v = [(-1, g, 0), (1, g, 0), (-1, -g, 0), (1, -g, 0), (0, -1, g), (0, 1, g), (0, -1, -g), (0, 1, -g),
+         (g, 0, -1), (g, 0, 1), (-g, 0, -1), (-g, 0, 1)]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
+         (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11),
+         (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    tris = np.array([[v[a], v[b], v[c]] for a, b, c in f], dtype=np.float64)
+    for _ in range(levels):
+        out = []
+        for a, b, c in tris:
+            ab, bc, ca = (a + b) / 2, (b + c) / 2, (c + a) / 2
+            out += [[a, ab, ca], [b, bc, ab], [c, ca, bc], [ab, bc, ca]]
+        tris = np.array(out)
+    tris = tris / np.linalg.norm(tris, axis=2, keepdims=True)
+    return tris * r * np.asarray(scale) + np.array([cx, cy, cz])
+
+
+def mesh_city(nx=48, ny=40, nz=16, h=2.0, n_buildings=6, n_trees=4, seed=0):
+    """Seeded closed meshes for the mesh resolver: prism buildings (4-8
+    sides, radius U[4, 10] m, height U[8, 0.8 lz] m, porosity 0) and
+    ellipsoidal canopies (radius U[3, 6] m, axes (r, r, 0.75 r), centre
+    height U[4, 10] m, porosity U[0.3, 0.8]), placed uniformly inside a 10 %
+    lateral margin; overlaps allowed.  Returns (triangles (n, 3, 3),
+    objects [(first, count, inside porosity)]).  Draw order per building:
+    x, y, radius, sides, angle, height; per canopy: x, y, radius, centre
+    height, porosity."""
+    rng = SplitMix64(seed)
+    lx, ly, lz = nx * h, ny * h, nz * h
+    meshes, objects, first = [], [], 0
+    for _ in range(n_buildings):
+        cx, cy = rng.uniform(0.1 * lx, 0.9 * lx), rng.uniform(0.1 * ly, 0.9 * ly)
+        r = rng.uniform(4.0, 10.0)
+        sides = rng.randint(4, 8)
+        ang = rng.uniform(0.0, 2 * np.pi)
+        H = rng.uniform(8.0, 0.8 * lz)
+        m = prism_mesh(cx, cy, r, sides, ang, 0.0, H)
+        meshes.append(m)
+        objects.append((first, len(m), 0.0))
+        first += len(m)
+    for _ in range(n_trees):
+        cx, cy = rng.uniform(0.1 * lx, 0.9 * lx), rng.uniform(0.1 * ly, 0.9 * ly)
+        r = rng.uniform(3.0, 6.0)
+        zc = rng.uniform(4.0, 10.0)
+        phi_in = rng.uniform(0.3, 0.8)
+        m = icosphere_mesh(cx, cy, zc, r, levels=1, scale=(1.0, 1.0, 0.75))
+        meshes.append(m)
+        objects.append((first, len(m), phi_in))
+        first += len(m)
+    return np.concatenate(meshes), objects
+
+
 def empty_domain(nx, ny, nz, h=1.0, u_ref=2.0, wind_dir_deg=0.0, ground_noslip=False,
                  loglaw=False) -> Scenario:
     phi = np.ones((nz, ny, nx))
