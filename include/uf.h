@@ -338,6 +338,25 @@ uf_status uf_substep(uf_grid* g, int which, int transpose, const void* const* in
 uf_status uf_design_to_phi(uf_grid* g, int nbox, const double* boxes, const double* theta, double width,
                            void* phi_out);
 
+/* Porosity from closed triangle meshes (Sec. 3, "Urban model resolving"):
+ * tris = 9 * ntri doubles (three vertices x, y, z per triangle, m, host
+ * array); object o is triangles [obj_first[o], obj_first[o] + obj_count[o])
+ * with porosity obj_phi[o] inside (0 for a building, the canopy's value for a
+ * tree).  A point is inside an object when it lies in the object's bounding
+ * box and a ray from it crosses the object's triangles an odd number of
+ * times (even-odd rule, Moller-Trumbore crossings, along the fixed direction
+ * (0.5741, 0.6219, 0.5327)); a cell's porosity is the mean over sub^3
+ * uniformly placed points of the minimum inside porosity of the objects
+ * containing the point, 1 in the open (the cut-cell volume fraction).  The
+ * decisions are made in FP64 with every operation rounded separately, so
+ * they are reproducible.  phi_out == NULL: sets the grid's porosity (as
+ * uf_set_porosity); else writes the dense field there (host or device).
+ * Allocates and frees device memory for the mesh; synchronises.  Errors:
+ * UF_ERR_ARG (NULL arrays, sub outside 1..16, a triangle range outside the
+ * mesh, a porosity outside [0, 1], a non-finite vertex). */
+uf_status uf_mesh_to_phi(uf_grid* g, int ntri, const double* tris, int nobj, const int* obj_first,
+                         const int* obj_count, const double* obj_phi, int sub, void* phi_out);
+
 /* Vector-Jacobian product of uf_design_to_phi: dJ/dtheta (host, 3*nbox
  * doubles) from dJ/dphi (dense cell field, grid precision, host or device).
  * Synchronises. */

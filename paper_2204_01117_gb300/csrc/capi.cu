@@ -19,6 +19,7 @@
 #include "../../include/uf.h"
 #include "grid_base.cuh"
 #include "adjoint_kernels.cuh"
+#include "mesh_kernels.cuh"
 
 namespace {
 
@@ -1627,6 +1628,85 @@ class GridImpl final : public uf_grid {
     return UF_OK;
   }
 
+  // ---------------------------------------------------- mesh resolver ----
+  // Porosity of closed triangle meshes (uf_mesh_to_phi): the mesh and the
+  // objects' bounding boxes are copied to device memory allocated for the
+  // call; the result goes to the grid's porosity (and drag coefficient) or
+  // to phi_out.
+  uf_status mesh_to_phi(int ntri, const double* tris, int nobj, const int* first, const int* count,
+                        const double* phi_in, int sub, void* phi_out) override {
+    if (ntri < 0 || nobj < 0 || (ntri > 0 && !tris) || (nobj > 0 && (!first || !count || !phi_in)))
+      return fail(UF_ERR_ARG, "NULL mesh arrays");
+    if (sub < 1 || sub > 16) return fail(UF_ERR_ARG, "sub-sampling must be 1..16 per axis");
+    std::vector<uf::MeshObject> obj(nobj);
+    for (int o = 0; o < nobj; ++o) {
+      if (first[o] < 0 || count[o] < 1 || (long long)first[o] + count[o] > ntri)
+        return fail(UF_ERR_ARG, "object " + std::to_string(o) + " has a triangle range outside the mesh");
+      if (!(phi_in[o] >= 0.0 && phi_in[o] <= 1.0))
+        return fail(UF_ERR_ARG, "object " + std::to_string(o) + " has a porosity outside [0, 1]");
+      uf::MeshObject& m = obj[o];
+      m.first = first[o];
+      m.count = count[o];
+      m.phi_in = phi_in[o];
+      for (int a = 0; a < 3; ++a) {
+        m.lo[a] = tris[9 * (size_t)m.first + a];
+        m.hi[a] = m.lo[a];
+      }
+      for (size_t e = (size_t)m.first; e < (size_t)m.first + m.count; ++e)
+        for (int c = 0; c < 3; ++c)
+          for (int a = 0; a < 3; ++a) {
+            const double x = tris[9 * e + 3 * c + a];
+            if (!std::isfinite(x)) return fail(UF_ERR_ARG, "non-finite vertex coordinate");
+            m.lo[a] = std::min(m.lo[a], x);
+            m.hi[a] = std::max(m.hi[a], x);
+          }
+      // cells whose closed box [i h, (i + 1) h] meets [lo, hi], per axis (a
+      // contiguous range; empty: clo > chi)
+      const int ext[3] = {d.nx, d.ny, d.nz};
+      for (int a = 0; a < 3; ++a) {
+        m.clo[a] = ext[a];
+        m.chi[a] = -1;
+        for (int c = 0; c < ext[a]; ++c) {
+          const double c0 = (double)c * d.h, c1 = (double)(c + 1) * d.h;
+          if (m.hi[a] < c0 || m.lo[a] > c1) continue;
+          m.clo[a] = std::min(m.clo[a], c);
+          m.chi[a] = std::max(m.chi[a], c);
+        }
+      }
+    }
+    double* dtri = nullptr;
+    uf::MeshObject* dobj = nullptr;
+    const size_t tb_tri = (size_t)std::max(ntri, 1) * 9 * sizeof(double);
+    const size_t tb_obj = (size_t)std::max(nobj, 1) * sizeof(uf::MeshObject);
+    UF_CUDA(cudaMalloc(&dtri, tb_tri));
+    cudaError_t e = cudaMalloc(&dobj, tb_obj);
+    if (e == cudaSuccess && ntri > 0)
+      e = cudaMemcpyAsync(dtri, tris, (size_t)ntri * 9 * sizeof(double), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && nobj > 0)
+      e = cudaMemcpyAsync(dobj, obj.data(), nobj * sizeof(uf::MeshObject), cudaMemcpyHostToDevice, stream);
+    T* dst = phi_out ? q : phi;
+    if (e == cudaSuccess) {
+      const long long cells = (long long)d.nx * d.ny * d.nz;
+      const unsigned blocks = (unsigned)((cells + uf::MESH_WARPS - 1) / uf::MESH_WARPS);
+      uf::k_mesh_phi<T><<<blocks, 32 * uf::MESH_WARPS, 0, stream>>>(d.nx, d.ny, d.nz, P.Pc, d.h, sub, dtri, dobj,
+                                                                     nobj, dst);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    cudaFree(dtri);
+    if (dobj) cudaFree(dobj);
+    UF_CUDA(e);
+    if (phi_out) {
+      uf_status s = copy_out(phi_out, q, d.nx, d.ny, d.nz, P.Pc);
+      if (s != UF_OK) return s;
+      UF_CUDA(cudaStreamSynchronize(stream));
+      return UF_OK;
+    }
+    uf::k_drag_coeff<T><<<(unsigned)((P.n_c + 255) / 256), 256, 0, stream>>>(phi, cc, P.n_c, d.Cd, d.a, d.b, d.e);
+    UF_CUDA(cudaGetLastError());
+    return UF_OK;
+  }
+
   // ------------------------------------------------------ sub-steps ------
   // One sub-step of the step, or its transpose, on dense inputs (test
   // support, uf_substep).  Works in a scratch block of four face sets and
@@ -2084,6 +2164,11 @@ uf_status uf_adjoint_run_ex(uf_grid* g, void* d_ws, size_t bytes, int nsteps, in
                             const uf_objective_desc* obj, void* dJ_dphi, double* J_out) {
   UF_NEED(g);
   return g->adjoint_run_ex(d_ws, bytes, nsteps, ckpt_every, obj, dJ_dphi, J_out);
+}
+uf_status uf_mesh_to_phi(uf_grid* g, int ntri, const double* tris, int nobj, const int* obj_first,
+                         const int* obj_count, const double* obj_phi, int sub, void* phi_out) {
+  UF_NEED(g);
+  return g->mesh_to_phi(ntri, tris, nobj, obj_first, obj_count, obj_phi, sub, phi_out);
 }
 uf_status uf_substep(uf_grid* g, int which, int transpose, const void* const* in, const void* const* cot,
                      void* const* out) {

@@ -60,6 +60,7 @@ struct uf_grid {
   virtual uf_status adjoint_run_ex(void*, size_t, int, int, const uf_objective_desc*, void*, double*) = 0;
   virtual uf_status step_vjp(void*, size_t, const void* const*, void* const*, void*) = 0;
   virtual uf_status substep(int, int, const void* const*, const void* const*, void* const*) = 0;
+  virtual uf_status mesh_to_phi(int, const double*, int, const int*, const int*, const double*, int, void*) = 0;
   virtual uf_status design_phi(int, const double*, const double*, double, void*) = 0;
   virtual uf_status design_vjp(int, const double*, const double*, double, const void*, double*) = 0;
   virtual uf_status get_tuning(uf_tuning*, int*) = 0;

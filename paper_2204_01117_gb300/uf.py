@@ -207,6 +207,8 @@ def load():
     lib.uf_adjoint_run_ex.restype = ip
     lib.uf_step_vjp.argtypes = [vp, vp, ctypes.c_size_t, P(vp), P(vp), vp]
     lib.uf_substep.argtypes = [vp, ip, ip, P(vp), P(vp), P(vp)]
+    lib.uf_mesh_to_phi.argtypes = [vp, ip, P(dp), ip, P(ip), P(ip), P(dp), ip, vp]
+    lib.uf_mesh_to_phi.restype = ip
     lib.uf_substep.restype = ip
     lib.uf_step_vjp.restype = ip
     lib.uf_design_to_phi.argtypes = [vp, ip, P(dp), P(dp), dp, vp]
@@ -576,6 +578,29 @@ class Grid:
             out = np.empty(self.shapes["phi"], dtype=self.np_dtype)
         optr, keep = self._arg(out)
         check(self.lib.uf_design_to_phi(self._h, b.shape[0], dptr(b), dptr(t), width, optr))
+        return out
+
+    def mesh_to_phi(self, tris, objects, sub: int = 4, set_porosity: bool = True, out=None):
+        """Porosity of closed triangle meshes (uf_mesh_to_phi): tris (n, 3, 3)
+        [m]; objects [(first triangle, count, inside porosity)].  Sets the
+        grid's porosity (default) or returns the field (in ``out`` when
+        given: CUDA tensor or numpy)."""
+        t = np.ascontiguousarray(np.asarray(tris, dtype=np.float64).reshape(-1, 9))
+        ob = list(objects)
+        first = np.ascontiguousarray([int(o[0]) for o in ob], dtype=np.int32)
+        count = np.ascontiguousarray([int(o[1]) for o in ob], dtype=np.int32)
+        pin = np.ascontiguousarray([float(o[2]) for o in ob], dtype=np.float64)
+        dptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        iptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        if set_porosity and out is None:
+            check(self.lib.uf_mesh_to_phi(self._h, t.shape[0], dptr(t), len(ob), iptr(first), iptr(count), dptr(pin),
+                                          sub, None))
+            return None
+        if out is None:
+            out = np.empty(self.shapes["phi"], dtype=self.np_dtype)
+        optr, keep = self._arg(out)
+        check(self.lib.uf_mesh_to_phi(self._h, t.shape[0], dptr(t), len(ob), iptr(first), iptr(count), dptr(pin), sub,
+                                      optr))
         return out
 
     def design_vjp(self, boxes, theta, width: float, dJ_dphi):
