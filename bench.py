@@ -149,15 +149,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# The headers the profiled solver kernels are compiled from (mg_fused.cuh and
+# what it includes); host-side launch code and other kernels are outside.
+DIGEST_HEADERS = ("mg_fused.cuh", "solver_kernels.cuh", "step_kernels.cuh", "uf_device.cuh")
+
+
 def source_digest():
-    """Digest of the device code of the single-grid kernels (the .cuh
-    headers); host-side launch code and the batched kernels are outside it."""
+    """Digest of the device code of the profiled solver kernels."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2204_01117_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith(".cuh"):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    for f in sorted(DIGEST_HEADERS):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
