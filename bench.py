@@ -716,6 +716,57 @@ def oracle_sample(max_seconds: float = 150.0, steps_wanted: int = 1):
     return rate, cores, sample, done, dt
 
 
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (x86: model name; Arm: the
+    implementer and part numbers), else the machine type."""
+    import platform
+    try:
+        info = open("/proc/cpuinfo").read()
+        m = re.search(r"^model name\s*:\s*(.+)$", info, re.M)
+        if m:
+            return m.group(1).strip()
+        imp = re.search(r"^CPU implementer\s*:\s*(\S+)", info, re.M)
+        part = re.search(r"^CPU part\s*:\s*(\S+)", info, re.M)
+        if imp and part:
+            return f"{platform.machine()} implementer {imp.group(1)} part {part.group(1)}"
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def oracle_single_box_run():
+    """The FP64 oracle on the single-box case (64 x 32 x 16, 100 steps after
+    its initial projection); prints one JSON line.  Run in a child process
+    so that OMP_NUM_THREADS takes effect."""
+    import oracle
+    from paper_2204_01117_gb300 import layouts
+    oracle.build()
+    sc = layouts.single_box()
+    o = oracle.Oracle(sc.nx, sc.ny, sc.nz, **sc.params())
+    o.set("phi", sc.phi)
+    o.init()
+    t0 = time.perf_counter()
+    o.run(100)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"value": sc.cells * 100 / dt, "seconds": dt,
+                      "threads": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}), flush=True)
+    return 0
+
+
+def oracle_thread_scaling():
+    """The single-box oracle run with 1 thread and with every core, each in
+    a child process."""
+    out = {}
+    for n in (1, os.cpu_count() or 1):
+        env = dict(os.environ, OMP_NUM_THREADS=str(n))
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-single-box"], env=env,
+                           capture_output=True, text=True, timeout=600)
+        if r.returncode != 0:
+            return {"error": r.stderr.strip().splitlines()[-1:] or ["failed"]}
+        out[f"threads_{n}"] = json.loads(r.stdout.strip().splitlines()[-1])
+    return out
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -836,7 +887,9 @@ def run_ours(args):
         line["batched"] = batched_leg(peak=peak, peak_kind=peak_kind)
     if not args.no_cpu_baseline and world == 1:
         rate, cores, sample, done, dt = oracle_sample(max_seconds=60.0, steps_wanted=1)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                                "cpu_model": cpu_model(),
+                                "single_box_100_steps": oracle_thread_scaling()}
     print(json.dumps(line), flush=True)
     if pg:
         pg.barrier()
@@ -860,9 +913,12 @@ def main():
     ap.add_argument("--large-grid", default="512x512x128", help="grid of --large (NXxNYxNZ)")
     ap.add_argument("--karman", action="store_true",
                     help="print the vortex-shedding validation table instead of the bench line")
+    ap.add_argument("--oracle-single-box", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--mesh", action="store_true",
                     help="print the mesh resolver's throughput instead of the bench line")
     args = ap.parse_args()
+    if args.oracle_single_box:
+        return oracle_single_box_run()
     if args.mesh:
         return run_mesh(args)
     if args.large:
