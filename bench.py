@@ -22,6 +22,12 @@ persistent launches, against the same instances stepped one after another
 Multi-GPU: replicas only (each rank advances its own independent grid; no
 collective in the data path), weak scaling; rank 0 prints one JSON line.
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+
+Other measurements, each printing its own JSON line instead of the bench
+line: ``--large`` (plain FP64 vs FP32 on the 512 x 512 x 128 block, with the
+adjoint over the last 100 steps), ``--karman`` (vortex-shedding validation
+against the Strouhal relation), ``--mesh`` (mesh resolver throughput) and
+``--preconditioners`` (CG iterations and step time per preconditioner).
 """
 from __future__ import annotations
 
