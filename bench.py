@@ -190,6 +190,19 @@ def ncu_traffic(kernel_label: str):
     return None
 
 
+def step_traffic(kernels: dict, ms_per_step: float, peak: float, cells: int) -> dict:
+    """Algorithmic bytes of one whole step -- the sum over an eagerly
+    launched step of each kernel's bytes per launch times its launches --
+    and their rate over the graph-replayed step time, against the HBM peak.
+    Never raises: a malformed profile gives {"error": ...}."""
+    try:
+        b = float(sum(k["bytes_per_launch"] * k["launches"] for k in kernels.values()))
+        gbs = b / (ms_per_step * 1e-3) / 1e9
+        return {"bytes": b, "bytes_per_cell": b / cells, "achieved": gbs, "unit": "GB/s", "frac": gbs / peak}
+    except Exception as e:   # noqa: BLE001 -- a report field, not a reason to lose the bench line
+        return {"error": repr(e)}
+
+
 # ---------------------------------------------------------------- adjoint leg
 
 def adjoint_leg():
@@ -881,7 +894,8 @@ def run_ours(args):
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"hbm_gbs of {peak_kind}",
                      "kernel_share_of_step": dom["total_ms"] / total_prof,
-                     "bytes_per_launch": dom["bytes_per_launch"], "avg_launch_us": avg_ms * 1e3},
+                     "bytes_per_launch": dom["bytes_per_launch"], "avg_launch_us": avg_ms * 1e3,
+                     "step": step_traffic(kernels, ms / args.steps, peak, sc.cells)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
         "gpu_launches": int(launches),
