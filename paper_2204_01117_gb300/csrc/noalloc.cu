@@ -137,13 +137,20 @@ extern "C" uf_status uf_poisson_solve_static(int nx, int ny, int nz, double wind
   uf::k_solve_reset<float><<<grid, blk, 0, s>>>(L, b, zc, partials, st);
   uf::k_cg_init<float><<<grid, blk, 0, s>>>(L, b, p, nullptr, zc, partials, st, 0, 0);
   uf::k_precond_simple<float><<<grid, blk, 0, s>>>(L, 2, w, z, zc, 0, partials, st, 0, 0);
+  // The host reads the convergence flag once per kPoll iterations.  Every
+  // iteration kernel returns at once when the flag is set (and the update
+  // kernel sets it at the iteration cap), so the launches queued past
+  // convergence change nothing.
+  constexpr int kPoll = 8;
   int conv = 0;
   e = cudaMemcpyAsync(&conv, &st->converged, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  for (int it = 0; e == cudaSuccess && !conv && it <= max_iter; ++it) {
-    uf::k_cg_direction_spmv<float><<<grid, blk, 0, s>>>(L, z, d0, d1, q, zc, partials, st);
-    uf::k_cg_update<float><<<grid, blk, 0, s>>>(L, p, d0, d1, q, zc, partials, st, 0, 0);
-    uf::k_precond_simple<float><<<grid, blk, 0, s>>>(L, 2, w, z, zc, 1, partials, st, 0, 0);
+  for (int it = 0; e == cudaSuccess && !conv && it <= max_iter; it += kPoll) {
+    for (int m = 0; m < kPoll; ++m) {
+      uf::k_cg_direction_spmv<float><<<grid, blk, 0, s>>>(L, z, d0, d1, q, zc, partials, st);
+      uf::k_cg_update<float><<<grid, blk, 0, s>>>(L, p, d0, d1, q, zc, partials, st, 0, 0);
+      uf::k_precond_simple<float><<<grid, blk, 0, s>>>(L, 2, w, z, zc, 1, partials, st, 0, 0);
+    }
     e = cudaMemcpyAsync(&conv, &st->converged, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }

@@ -307,19 +307,39 @@ def _ptr(buf, dtype):
 STATIC_MAX_CELLS = 800000
 
 
+_static_streams = {}
+
+
 def poisson_solve_static(b, p, wind_dir_deg: float = 0.0, tol: float = 1e-7, max_iter: int = 5000, stream=None):
     """uf_poisson_solve_static on dense float32 CUDA tensors b (in) and p (in/out).
 
     The solve allocates no device memory: its scratch is a fixed array inside
-    the library (see include/uf.h).  Returns (iterations, relative residual)."""
+    the library (see include/uf.h).  b and p must live on the current CUDA
+    device, whose copy of the scratch the call uses.  The C entry point needs
+    a created (non-default) stream; with stream=None the call runs on one
+    such stream kept per device, after the work already queued on the
+    current stream.  The call returns when the solve is done.  Returns
+    (iterations, relative residual)."""
     import torch
     lib = load()
     if b.dtype != torch.float32 or p.dtype != torch.float32 or not b.is_cuda or not p.is_cuda:
         raise TypeError("b and p must be float32 CUDA tensors")
     if not (b.is_contiguous() and p.is_contiguous()) or b.shape != p.shape or b.dim() != 3:
         raise TypeError("b and p must be contiguous (nz, ny, nx) tensors of the same shape")
+    dev = torch.cuda.current_device()
+    if b.device.index != dev or p.device.index != dev:
+        raise TypeError(f"b and p must be on the current CUDA device (cuda:{dev}); "
+                        f"got {b.device} and {p.device}")
     nz, ny, nx = b.shape
-    s = stream if stream is not None else torch.cuda.current_stream()
+    if stream is None:
+        s = _static_streams.get(dev)
+        if s is None:
+            s = _static_streams[dev] = torch.cuda.Stream(device=dev)
+        s.wait_stream(torch.cuda.current_stream(dev))
+    else:
+        s = stream
+    if s.cuda_stream == 0:
+        raise TypeError("poisson_solve_static needs a created CUDA stream, not the legacy default stream")
     it, rel = ctypes.c_int(), ctypes.c_double()
     check(lib.uf_poisson_solve_static(nx, ny, nz, wind_dir_deg, ctypes.c_void_p(b.data_ptr()),
                                       ctypes.c_void_p(p.data_ptr()), tol, max_iter,
