@@ -378,6 +378,12 @@ typedef struct {
                                  level or below the automatic one are clamped */
   int march_zc[UF_MAX_LEVELS];/* z planes per block of level l; 0 = automatic;
                                  otherwise even, 2..64 */
+  int advect_zc;              /* z planes per block of the fused MacCormack
+                                 advection; 0 = automatic (16), else 1..64 */
+  int advect_unfused;         /* 1: run the advection as its two separate
+                                 passes (forward, backward) instead of the
+                                 fused kernel; both give the same values bit
+                                 for bit.  0 = fused (default) */
 } uf_tuning;
 
 /* The knobs in use, resolved (no zeros).  levels: number of MG levels. */

@@ -19,6 +19,7 @@
 #include "../../include/uf.h"
 #include "grid_base.cuh"
 #include "adjoint_kernels.cuh"
+#include "advect_fused.cuh"
 #include "mesh_kernels.cuh"
 
 namespace {
@@ -326,6 +327,12 @@ class GridImpl final : public uf_grid {
   T* dtT;
   uf::SolveState* st;
   cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
+  // the same step with the intermediate fields the adjoint tapes (phi^ of
+  // the fused advection) written out as well
+  cudaGraphExec_t tape_exec[2] = {nullptr, nullptr};
+  bool taping = false;
+  int advect_unfused = 0;   // tuning: 1 runs the two-kernel MacCormack form
+  int advect_zc_tuned = 0;  // tuning: z planes per block of the fused advection (0: automatic)
   cudaGraphExec_t init_exec = nullptr, solve_exec = nullptr;
   int parity = 0;
   bool have_state = false;
@@ -333,6 +340,7 @@ class GridImpl final : public uf_grid {
 
   ~GridImpl() override {
     for (auto& e : step_exec) if (e) cudaGraphExecDestroy(e);
+    for (auto& e : tape_exec) if (e) cudaGraphExecDestroy(e);
     for (auto& e : pool) cudaEventDestroy(e);
     if (init_exec) cudaGraphExecDestroy(init_exec);
     if (solve_exec) cudaGraphExecDestroy(solve_exec);
@@ -512,6 +520,7 @@ class GridImpl final : public uf_grid {
     };
     lim((const void*)uf::k_mg_tail<T, uf::SM_JACOBI>);
     lim((const void*)uf::k_mg_tail<T, uf::SM_RBGS>);
+    lim((const void*)uf::k_advect_fused<T>);
     return e;
   }
 
@@ -715,6 +724,13 @@ class GridImpl final : public uf_grid {
     return A;
   }
 
+  // Fused advection: 32 x 8 columns, zc planes per block (16 unless tuned).
+  dim3 advect_grid(int* zc) const {
+    const int z = advect_zc_tuned > 0 ? advect_zc_tuned : 16;
+    *zc = z;
+    return dim3((d.nx + uf::MX - 1) / uf::MX, (d.ny + uf::MY - 1) / uf::MY, (d.nz + z - 1) / z);
+  }
+
   void rec_momentum(cudaStream_t s, const T* kin, const T* oin) {
     const dim3 blk(uf::BX, uf::BY);
     const double faces = 3 * N() * tb(), cells = N() * tb();
@@ -726,8 +742,18 @@ class GridImpl final : public uf_grid {
       [&] { uf::k_eddy_viscosity<T><<<plane_grid(d.nx, d.ny, d.nz), blk, 0, s>>>(sp, u, v, w, kin, oin, nut); });
     const uf::AdvectArgs<T> A = advect_args();
     const dim3 ga = plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1);
-    L(s, "advect_forward", 2 * faces, [&] { uf::k_advect_forward<T><<<ga, blk, 0, s>>>(A); });
-    L(s, "advect_backward", 3 * faces, [&] { uf::k_advect_backward<T><<<ga, blk, 0, s>>>(A); });
+    if (!advect_unfused) {
+      uf::AdvectArgs<T> Af = A;
+      if (!taping) Af.uh = Af.vh = Af.wh = nullptr;
+      int zc;
+      const dim3 gf = advect_grid(&zc);
+      L(s, "advect_fused", 2 * faces, [&] {
+        uf::k_advect_fused<T><<<gf, uf::MT, uf::advect_fused_smem_total<T>(), s>>>(Af, zc);
+      });
+    } else {
+      L(s, "advect_forward", 2 * faces, [&] { uf::k_advect_forward<T><<<ga, blk, 0, s>>>(A); });
+      L(s, "advect_backward", 3 * faces, [&] { uf::k_advect_backward<T><<<ga, blk, 0, s>>>(A); });
+    }
     L(s, "diffuse", 2 * faces + cells, [&] { uf::k_diffuse<T><<<ga, blk, 0, s>>>(sp, ut, vt, wt, nut, u2, v2, w2); });
     L(s, "drag_bc", 2 * faces + cells, [&] { uf::k_drag_bc<T><<<ga, blk, 0, s>>>(sp, u2, v2, w2, cc, u, v, w); });
     int zc;
@@ -933,8 +959,10 @@ class GridImpl final : public uf_grid {
 
   // Runs one step from the current state and tapes it into slot t.
   uf_status tape_step(T* t, const AdjLayout& A) {
+    uf_status bs = build_tape_graphs();
+    if (bs != UF_OK) return bs;
     UF_CUDA(save_state(t, A));
-    UF_CUDA(cudaGraphLaunch(step_exec[parity], stream));
+    UF_CUDA(cudaGraphLaunch(tape_exec[parity], stream));
     parity ^= 1;
     UF_CUDA(copy_cell(t + A.s_nut, nut));
     UF_CUDA(copy_faces(faces_at(t + A.s_uh), uh, vh, wh));
@@ -1212,9 +1240,30 @@ class GridImpl final : public uf_grid {
     return UF_OK;
   }
 
+  // The taping variant of the step graphs (the same kernels and arithmetic;
+  // the fused kernels also write the intermediate fields the adjoint reads).
+  uf_status build_tape_graphs() {
+    for (int par = 0; par < 2; ++par) {
+      if (tape_exec[par]) continue;
+      T* kin = kb[par];
+      T* oin = ob[par];
+      T* kout = kb[1 - par];
+      T* oout = ob[1 - par];
+      int nf, ns, ni;
+      taping = true;
+      uf_status s = capture(&tape_exec[par], [&](cudaStream_t st2) { rec_momentum(st2, kin, oin); },
+                            [&](cudaStream_t st2) { rec_post(st2, kin, oin, kout, oout); }, &nf, &ns, &ni);
+      taping = false;
+      if (s != UF_OK) return s;
+    }
+    return UF_OK;
+  }
+
   // Drops every captured graph (after a change of the launch tuning).
   void drop_graphs() {
     for (auto& e : step_exec)
+      if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+    for (auto& e : tape_exec)
       if (e) { cudaGraphExecDestroy(e); e = nullptr; }
     if (init_exec) { cudaGraphExecDestroy(init_exec); init_exec = nullptr; }
     if (solve_exec) { cudaGraphExecDestroy(solve_exec); solve_exec = nullptr; }
@@ -1243,17 +1292,26 @@ class GridImpl final : public uf_grid {
       march_grid(l, &zc);
       t->march_zc[l] = d.precond == UF_PRECOND_MG ? zc : 0;
     }
+    int azc;
+    advect_grid(&azc);
+    t->advect_zc = azc;
+    t->advect_unfused = advect_unfused;
     if (levels) *levels = P.nl;
     return UF_OK;
   }
 
   uf_status set_tuning(const uf_tuning* t) override {
-    if (t)
+    if (t) {
       for (int l = 0; l < UF_MAX_LEVELS; ++l) {
         const int z = t->march_zc[l];
         if (z != 0 && (z < 2 || z > 64 || (z & 1))) return fail(UF_ERR_ARG, "march_zc must be 0 or even in [2, 64]");
       }
+      if (t->advect_zc < 0 || t->advect_zc > 64) return fail(UF_ERR_ARG, "advect_zc must be in [0, 64]");
+      if (t->advect_unfused != 0 && t->advect_unfused != 1) return fail(UF_ERR_ARG, "advect_unfused must be 0 or 1");
+    }
     drop_graphs();
+    advect_zc_tuned = t ? t->advect_zc : 0;
+    advect_unfused = t ? t->advect_unfused : 0;
     for (int l = 0; l < uf::MAX_LEVELS; ++l) march_zc_tuned[l] = t ? t->march_zc[l] : 0;
     return set_tail_level(t && t->tail_level > 0 ? t->tail_level : P.auto_tail_level);
   }
@@ -1291,6 +1349,8 @@ class GridImpl final : public uf_grid {
       std::memset(&t, 0, sizeof(t));
       t.tail_level = c.lt;
       for (int l = 0; l < UF_MAX_LEVELS; ++l) t.march_zc[l] = c.zc;
+      t.advect_zc = advect_zc_tuned;       // the solve's candidates keep the step's other knobs
+      t.advect_unfused = advect_unfused;
       rs = set_tuning(&t);
       if (rs != UF_OK) break;
       cudaGraphExec_t ex = nullptr;

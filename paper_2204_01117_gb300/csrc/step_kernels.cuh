@@ -150,6 +150,33 @@ __device__ __forceinline__ bool axis_inside(int base, T off, int n) {
   return f >= 0 && (f < n - 1 || (f == n - 1 && off == fo));
 }
 
+// Trilinear interpolation of the 8 corner values f[a + 2b + 4c] with
+// weights (ta, tb, tc), as nested lerps along x, then y, then z; optionally
+// the range of the 8 values.  Every semi-Lagrangian sample of the step goes
+// through this one expression, whatever memory the corners come from.
+template <typename T, bool RANGE>
+__device__ __forceinline__ T trilerp(const T (&f)[8], T ta, T tb, T tc, T* mn, T* mx) {
+  if (RANGE) {
+    *mn = fmin(fmin(fmin(f[0], f[1]), fmin(f[2], f[3])), fmin(fmin(f[4], f[5]), fmin(f[6], f[7])));
+    *mx = fmax(fmax(fmax(f[0], f[1]), fmax(f[2], f[3])), fmax(fmax(f[4], f[5]), fmax(f[6], f[7])));
+  }
+  const T x00 = lerp_(f[0], f[1], ta), x10 = lerp_(f[2], f[3], ta);
+  const T x01 = lerp_(f[4], f[5], ta), x11 = lerp_(f[6], f[7], ta);
+  return lerp_(lerp_(x00, x10, tb), lerp_(x01, x11, tb), tc);
+}
+
+// The 8 corners of a sample from global memory.
+template <typename T>
+__device__ __forceinline__ void corners_global(const T* __restrict__ F, Lattice L, int i0, int i1, int j0, int j1,
+                                               int k0, int k1, T (&f)[8]) {
+  const size_t r00 = (size_t)L.P * ((size_t)j0 + (size_t)L.Ly * k0);
+  const size_t r10 = (size_t)L.P * ((size_t)j1 + (size_t)L.Ly * k0);
+  const size_t r01 = (size_t)L.P * ((size_t)j0 + (size_t)L.Ly * k1);
+  const size_t r11 = (size_t)L.P * ((size_t)j1 + (size_t)L.Ly * k1);
+  f[0] = F[r00 + i0]; f[1] = F[r00 + i1]; f[2] = F[r10 + i0]; f[3] = F[r10 + i1];
+  f[4] = F[r01 + i0]; f[5] = F[r01 + i1]; f[6] = F[r11 + i0]; f[7] = F[r11 + i1];
+}
+
 // Trilinear sample at lattice coordinates (ia + oa, ib + ob, ic + oc),
 // clamped to the lattice; optionally the range of the 8 values used.
 template <typename T, bool RANGE>
@@ -160,19 +187,9 @@ __device__ __forceinline__ T sample(const T* __restrict__ F, Lattice L, int ia, 
   axis_cell(ia, oa, L.Lx, i0, i1, ta);
   axis_cell(ib, ob, L.Ly, j0, j1, tb);
   axis_cell(ic, oc, L.Lz, k0, k1, tc);
-  const size_t r00 = (size_t)L.P * ((size_t)j0 + (size_t)L.Ly * k0);
-  const size_t r10 = (size_t)L.P * ((size_t)j1 + (size_t)L.Ly * k0);
-  const size_t r01 = (size_t)L.P * ((size_t)j0 + (size_t)L.Ly * k1);
-  const size_t r11 = (size_t)L.P * ((size_t)j1 + (size_t)L.Ly * k1);
-  const T f000 = F[r00 + i0], f100 = F[r00 + i1], f010 = F[r10 + i0], f110 = F[r10 + i1];
-  const T f001 = F[r01 + i0], f101 = F[r01 + i1], f011 = F[r11 + i0], f111 = F[r11 + i1];
-  if (RANGE) {
-    *mn = fmin(fmin(fmin(f000, f100), fmin(f010, f110)), fmin(fmin(f001, f101), fmin(f011, f111)));
-    *mx = fmax(fmax(fmax(f000, f100), fmax(f010, f110)), fmax(fmax(f001, f101), fmax(f011, f111)));
-  }
-  const T x00 = lerp_(f000, f100, ta), x10 = lerp_(f010, f110, ta);
-  const T x01 = lerp_(f001, f101, ta), x11 = lerp_(f011, f111, ta);
-  return lerp_(lerp_(x00, x10, tb), lerp_(x01, x11, tb), tc);
+  T f[8];
+  corners_global(F, L, i0, i1, j0, j1, k0, k1, f);
+  return trilerp<T, RANGE>(f, ta, tb, tc, mn, mx);
 }
 
 template <typename T>
