@@ -375,7 +375,8 @@ typedef struct {
   int tail_level;             /* first level of the tail; 0 = automatic (the
                                  shallowest level whose levels fit 64 KB of
                                  shared memory); values above the coarsest
-                                 level or below the automatic one are clamped */
+                                 level, or below the shallowest level whose
+                                 levels fit 220 KB, are clamped */
   int march_zc[UF_MAX_LEVELS];/* z planes per block of level l; 0 = automatic;
                                  otherwise even, 2..64 */
   int advect_zc;              /* z planes per block of the fused MacCormack

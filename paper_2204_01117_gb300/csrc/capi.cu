@@ -45,6 +45,7 @@ constexpr int kPartials = 8192;      // doubles per partials buffer
 constexpr int kDtBlocks = 1024;
 constexpr int kTargetBlocks = 2048;  // blocks of reducing cell kernels
 constexpr size_t kTailSmemBudget = 64 * 1024;
+constexpr size_t kTailSmemMax = 220 * 1024;   // below the 227 KB per-block opt-in of sm_103a
 
 struct LevelDims {
   int nx, ny, nz, P;
@@ -126,6 +127,7 @@ struct Plan {
   size_t u, v, w, uh, vh, wh, ut, vt, wt, u2, v2, w2, k0, k1, o0, o1, cc, phi, nut, p, pd, gd, b, r, r2, z, q, d0, d1;
   int nl;                  // multigrid levels in use (1 without MG)
   int auto_tail_level;     // shallowest level whose tail fits the shared-memory budget
+  int min_tail_level;      // shallowest level whose tail fits one block's shared memory
   int tail_level;          // first level run by the shared-memory tail kernel
   size_t tail_smem;        // its dynamic shared memory (bytes)
   size_t tail_cr_off;      // byte offset of the coarsest solve's FP64 right-hand side in it
@@ -176,10 +178,15 @@ Plan make_plan(const uf_grid_desc* d) {
   // arrays per level fit the shared-memory budget
   P.nl = (int)nl;
   P.auto_tail_level = (int)nl - 1;
+  P.min_tail_level = (int)nl - 1;
   if (mg) {
     for (int l = (int)nl - 1; l >= 1; --l) {
       if (tail_bytes(P, l) > kTailSmemBudget) break;
       P.auto_tail_level = l;
+    }
+    for (int l = (int)nl - 1; l >= 1; --l) {
+      if (tail_bytes(P, l) > kTailSmemMax) break;
+      P.min_tail_level = l;
     }
   }
   plan_tail(P, P.auto_tail_level);
@@ -1274,7 +1281,7 @@ class GridImpl final : public uf_grid {
   // Tail starting at level lt (clamped to [automatic, coarsest]).
   uf_status set_tail_level(int lt) {
     if (d.precond != UF_PRECOND_MG) return UF_OK;
-    lt = std::min(std::max(lt, P.auto_tail_level), P.nl - 1);
+    lt = std::min(std::max(lt, P.min_tail_level), P.nl - 1);
     plan_tail(P, lt);
     for (int l = 0; l < P.nl; ++l) tail.off[l] = P.tail_off[l];
     tail.lt = lt;

@@ -537,6 +537,20 @@ __global__ void __launch_bounds__(FT) k_mg_up(Level<T> F, Level<T> C, SmoothW<T>
 constexpr int TAIL_T = 1024;
 constexpr int MAX_LEVELS = 16;
 
+// The cells of an nx x ny x nz tail level spread over the TAIL_T threads
+// laid out 16 x 16 x 4 (x fastest): thread (tx, ty, tz) takes i = tx, tx +
+// 16, ..., j = ty, ty + 16, ..., k = tz, tz + 4, ...  No division by the
+// level's extents (an integer division by a run-time value is a long
+// instruction sequence, and the tail would take several per cell and pass).
+template <typename F>
+__device__ __forceinline__ void tail_cells(int nx, int ny, int nz, F f) {
+  static_assert(TAIL_T == 16 * 16 * 4, "tail thread layout");
+  const int tx = threadIdx.x & 15, ty = (threadIdx.x >> 4) & 15, tz = threadIdx.x >> 8;
+  for (int k = tz; k < nz; k += 4)
+    for (int j = ty; j < ny; j += 16)
+      for (int i = tx; i < nx; i += 16) f(i, j, k);
+}
+
 template <typename T>
 struct TailArgs {
   Level<T> lv[MAX_LEVELS];
@@ -573,11 +587,9 @@ __device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, const SmoothW
     int X, P, NB;
     geom(A.lt, X, P, NB);
     T* r = S + A.off[A.lt];
-    const int n = L.nx * L.ny * L.nz;
-    for (int e = tid; e < n; e += TAIL_T) {
-      const int i = e % L.nx, j = (e / L.nx) % L.ny, k = e / (L.nx * L.ny);
+    tail_cells(L.nx, L.ny, L.nz, [&](int i, int j, int k) {
       r[(i + 1) + X * (j + 1) + P * (k + 1)] = L.r[lidx(L, i, j, k)];
-    }
+    });
   }
   __syncthreads();
   for (int m = A.lt; m < A.nl - 1; ++m) {
@@ -589,24 +601,19 @@ __device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, const SmoothW
     T* r = S + A.off[m];
     T* a = r + NB;
     T* u = a + NB;   // u holds r/D during the down leg
-    const int n = L.nx * L.ny * L.nz;
-    for (int e = tid; e < n; e += TAIL_T) {
-      const int i = e % L.nx, j = (e / L.nx) % L.ny, k = e / (L.nx * L.ny);
+    tail_cells(L.nx, L.ny, L.nz, [&](int i, int j, int k) {
       const int b = (i + 1) + X * (j + 1) + P * (k + 1);
       u[b] = r[b] * rdiag(diag_of(L, i, j, k));
-    }
+    });
     __syncthreads();
-    for (int e = tid; e < n; e += TAIL_T) {
-      const int i = e % L.nx, j = (e / L.nx) % L.ny, k = e / (L.nx * L.ny);
+    tail_cells(L.nx, L.ny, L.nz, [&](int i, int j, int k) {
       const int b = (i + 1) + X * (j + 1) + P * (k + 1);
       const T s = L.wx * (u[b - 1] + u[b + 1]) + L.wy * (u[b - X] + u[b + X]) + L.wz * (u[b - P] + u[b + P]);
       a[b] = presmooth<SM>(u[b], s, diag_of(L, i, j, k), W, ((i + j + k) & 1) == 0);
-    }
+    });
     __syncthreads();
     T* rc = S + A.off[m + 1];
-    const int nc = Cc.nx * Cc.ny * Cc.nz;
-    for (int e = tid; e < nc; e += TAIL_T) {
-      const int ci = e % Cc.nx, cj = (e / Cc.nx) % Cc.ny, ck = e / (Cc.nx * Cc.ny);
+    tail_cells(Cc.nx, Cc.ny, Cc.nz, [&](int ci, int cj, int ck) {
       const int i0 = L.cx ? 2 * ci : ci, i1 = L.cx ? min(2 * ci + 1, L.nx - 1) : ci;
       const int j0 = L.cy ? 2 * cj : cj, j1 = L.cy ? min(2 * cj + 1, L.ny - 1) : cj;
       const int k0 = L.cz ? 2 * ck : ck, k1 = L.cz ? min(2 * ck + 1, L.nz - 1) : ck;
@@ -619,7 +626,7 @@ __device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, const SmoothW
             s += r[b] - diag_of(L, ii, jj, kk) * a[b] + nb;
           }
       rc[(ci + 1) + CX * (cj + 1) + CP * (ck + 1)] = s;
-    }
+    });
     __syncthreads();
   }
   // coarsest level: a = A^-1 r with the FP64 dense inverse.  r is first
@@ -635,10 +642,9 @@ __device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, const SmoothW
     T* a = S + A.off[m] + NB;
     const int n = A.n_coarse;
     double* cr = reinterpret_cast<double*>(smem_raw + A.cr_off);
-    for (int c = tid; c < n; c += TAIL_T) {
-      const int i = c % L.nx, j = (c / L.nx) % L.ny, k = c / (L.nx * L.ny);
-      cr[c] = (double)r[(i + 1) + X * (j + 1) + P * (k + 1)];
-    }
+    tail_cells(L.nx, L.ny, L.nz, [&](int i, int j, int k) {
+      cr[i + L.nx * (j + L.ny * k)] = (double)r[(i + 1) + X * (j + 1) + P * (k + 1)];
+    });
     __syncthreads();
     constexpr int G = 8;
     const int lane = tid % G;
@@ -666,26 +672,22 @@ __device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, const SmoothW
     T* a = r + NB;
     T* u = a + NB;
     const T* ec = S + A.off[m + 1] + CNB;
-    const int n = L.nx * L.ny * L.nz;
-    for (int e = tid; e < n; e += TAIL_T) {   // t = x + P e (in place)
-      const int i = e % L.nx, j = (e / L.nx) % L.ny, k = e / (L.nx * L.ny);
+    tail_cells(L.nx, L.ny, L.nz, [&](int i, int j, int k) {   // t = x + P e (in place)
       const int pi = L.cx ? i >> 1 : i, pj = L.cy ? j >> 1 : j, pk = L.cz ? k >> 1 : k;
       a[(i + 1) + X * (j + 1) + P * (k + 1)] += ec[(pi + 1) + CX * (pj + 1) + CP * (pk + 1)];
-    }
+    });
     __syncthreads();
-    for (int e = tid; e < n; e += TAIL_T) {
-      const int i = e % L.nx, j = (e / L.nx) % L.ny, k = e / (L.nx * L.ny);
+    tail_cells(L.nx, L.ny, L.nz, [&](int i, int j, int k) {
       const int b = (i + 1) + X * (j + 1) + P * (k + 1);
       const T s = L.wx * (a[b - 1] + a[b + 1]) + L.wy * (a[b - X] + a[b + X]) + L.wz * (a[b - P] + a[b + P]);
       u[b] = relax<SM>(a[b], r[b], s, diag_of(L, i, j, k), W.w1, ((i + j + k) & 1) == 1);
-    }
+    });
     __syncthreads();
-    for (int e = tid; e < n; e += TAIL_T) {
-      const int i = e % L.nx, j = (e / L.nx) % L.ny, k = e / (L.nx * L.ny);
+    tail_cells(L.nx, L.ny, L.nz, [&](int i, int j, int k) {
       const int b = (i + 1) + X * (j + 1) + P * (k + 1);
       const T s = L.wx * (u[b - 1] + u[b + 1]) + L.wy * (u[b - X] + u[b + X]) + L.wz * (u[b - P] + u[b + P]);
       a[b] = relax<SM>(u[b], r[b], s, diag_of(L, i, j, k), W.w2, ((i + j + k) & 1) == 0);
-    }
+    });
     __syncthreads();
   }
   {
@@ -693,11 +695,9 @@ __device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, const SmoothW
     int X, P, NB;
     geom(A.lt, X, P, NB);
     const T* a = S + A.off[A.lt] + NB;
-    const int n = L.nx * L.ny * L.nz;
-    for (int e = tid; e < n; e += TAIL_T) {
-      const int i = e % L.nx, j = (e / L.nx) % L.ny, k = e / (L.nx * L.ny);
+    tail_cells(L.nx, L.ny, L.nz, [&](int i, int j, int k) {
       L.t[lidx(L, i, j, k)] = a[(i + 1) + X * (j + 1) + P * (k + 1)];
-    }
+    });
   }
 }
 
