@@ -371,6 +371,8 @@ uf_status uf_design_vjp(uf_grid* g, int nbox, const double* boxes, const double*
  * depth).  Other preconditioners ignore them.  Results stay equal up to the
  * order of FP64 partial sums. */
 #define UF_MAX_LEVELS 16
+#define UF_UNFUSED_ADVECT 1
+#define UF_UNFUSED_MOMENTUM 2
 typedef struct {
   int tail_level;             /* first level of the tail; 0 = automatic (the
                                  shallowest level whose levels fit 64 KB of
@@ -381,10 +383,13 @@ typedef struct {
                                  otherwise even, 2..64 */
   int advect_zc;              /* z planes per block of the fused MacCormack
                                  advection; 0 = automatic (16), else 1..64 */
-  int advect_unfused;         /* 1: run the advection as its two separate
-                                 passes (forward, backward) instead of the
-                                 fused kernel; both give the same values bit
-                                 for bit.  0 = fused (default) */
+  int unfused;                /* bit mask of the step's fused kernels to run as
+                                 their separate sub-step kernels instead:
+                                 1 = the advection as its two passes
+                                 (forward, backward); 2 = diffusion, drag +
+                                 BCs and the pressure right-hand side as
+                                 three kernels.  Both forms give the same
+                                 values bit for bit.  0 = all fused (default) */
 } uf_tuning;
 
 /* The knobs in use, resolved (no zeros).  levels: number of MG levels. */

@@ -20,6 +20,7 @@
 #include "grid_base.cuh"
 #include "adjoint_kernels.cuh"
 #include "advect_fused.cuh"
+#include "momentum_fused.cuh"
 #include "mesh_kernels.cuh"
 
 namespace {
@@ -338,7 +339,7 @@ class GridImpl final : public uf_grid {
   // the fused advection) written out as well
   cudaGraphExec_t tape_exec[2] = {nullptr, nullptr};
   bool taping = false;
-  int advect_unfused = 0;   // tuning: 1 runs the two-kernel MacCormack form
+  int unfused = 0;          // tuning: bit mask of fused kernels run as their sub-step kernels
   int advect_zc_tuned = 0;  // tuning: z planes per block of the fused advection (0: automatic)
   cudaGraphExec_t init_exec = nullptr, solve_exec = nullptr;
   int parity = 0;
@@ -455,8 +456,8 @@ class GridImpl final : public uf_grid {
       tail.nl = (int)nl;
       tail.ainv = ainv;
       tail.n_coarse = P.coarse_n;
-      UF_CUDA(set_smem_limits());
     }
+    UF_CUDA(set_smem_limits());   // every grid: the fused step kernels need more than 48 KB
     if (d.precond == UF_PRECOND_MG) {
       const LevelDims& cl = P.levels.back();
       const uf::Level<T>& L = lv.back();
@@ -522,12 +523,16 @@ class GridImpl final : public uf_grid {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess && P.tail_smem > (size_t)optin) return cudaErrorInvalidValue;
-    auto lim = [&](const void* f) {
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    auto lim = [&](const void* f) {   // the opt-in maximum less the kernel's static shared memory
+      cudaFuncAttributes fa;
+      if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, f);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
     };
     lim((const void*)uf::k_mg_tail<T, uf::SM_JACOBI>);
     lim((const void*)uf::k_mg_tail<T, uf::SM_RBGS>);
     lim((const void*)uf::k_advect_fused<T>);
+    lim((const void*)uf::k_momentum_fused<T>);
     return e;
   }
 
@@ -749,7 +754,7 @@ class GridImpl final : public uf_grid {
       [&] { uf::k_eddy_viscosity<T><<<plane_grid(d.nx, d.ny, d.nz), blk, 0, s>>>(sp, u, v, w, kin, oin, nut); });
     const uf::AdvectArgs<T> A = advect_args();
     const dim3 ga = plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1);
-    if (!advect_unfused) {
+    if (!(unfused & UF_UNFUSED_ADVECT)) {
       uf::AdvectArgs<T> Af = A;
       if (!taping) Af.uh = Af.vh = Af.wh = nullptr;
       int zc;
@@ -761,12 +766,24 @@ class GridImpl final : public uf_grid {
       L(s, "advect_forward", 2 * faces, [&] { uf::k_advect_forward<T><<<ga, blk, 0, s>>>(A); });
       L(s, "advect_backward", 3 * faces, [&] { uf::k_advect_backward<T><<<ga, blk, 0, s>>>(A); });
     }
-    L(s, "diffuse", 2 * faces + cells, [&] { uf::k_diffuse<T><<<ga, blk, 0, s>>>(sp, ut, vt, wt, nut, u2, v2, w2); });
-    L(s, "drag_bc", 2 * faces + cells, [&] { uf::k_drag_bc<T><<<ga, blk, 0, s>>>(sp, u2, v2, w2, cc, u, v, w); });
     int zc;
     const dim3 gr = chunk_grid(d.nx, d.ny, d.nz, &zc);
-    L(s, "pressure_rhs", faces + cells,
-      [&] { uf::k_pressure_rhs<T><<<gr, blk, 0, s>>>(sp, u, v, w, b, zc, partials, st); });
+    if (!(unfused & UF_UNFUSED_MOMENTUM)) {
+      // one pass: u~, nu_t, c -> u3 (every face), b
+      uf::MomentumArgs<T> M;
+      M.p = sp; M.ut = ut; M.vt = vt; M.wt = wt; M.nut = nut; M.cc = cc;
+      M.u = u; M.v = v; M.w = w; M.b = b;
+      M.u2t = taping ? u2 : nullptr; M.v2t = taping ? v2 : nullptr; M.w2t = taping ? w2 : nullptr;
+      M.zc = zc; M.partials = partials; M.st = st;
+      L(s, "momentum_fused", faces + 2 * cells + faces + cells, [&] {
+        uf::k_momentum_fused<T><<<gr, uf::MT, uf::momentum_fused_smem<T>(), s>>>(M);
+      });
+    } else {
+      L(s, "diffuse", 2 * faces + cells, [&] { uf::k_diffuse<T><<<ga, blk, 0, s>>>(sp, ut, vt, wt, nut, u2, v2, w2); });
+      L(s, "drag_bc", 2 * faces + cells, [&] { uf::k_drag_bc<T><<<ga, blk, 0, s>>>(sp, u2, v2, w2, cc, u, v, w); });
+      L(s, "pressure_rhs", faces + cells,
+        [&] { uf::k_pressure_rhs<T><<<gr, blk, 0, s>>>(sp, u, v, w, b, zc, partials, st); });
+    }
   }
 
   void rec_post(cudaStream_t s, const T* kin, const T* oin, T* kout, T* oout) {
@@ -1302,7 +1319,7 @@ class GridImpl final : public uf_grid {
     int azc;
     advect_grid(&azc);
     t->advect_zc = azc;
-    t->advect_unfused = advect_unfused;
+    t->unfused = unfused;
     if (levels) *levels = P.nl;
     return UF_OK;
   }
@@ -1314,11 +1331,11 @@ class GridImpl final : public uf_grid {
         if (z != 0 && (z < 2 || z > 64 || (z & 1))) return fail(UF_ERR_ARG, "march_zc must be 0 or even in [2, 64]");
       }
       if (t->advect_zc < 0 || t->advect_zc > 64) return fail(UF_ERR_ARG, "advect_zc must be in [0, 64]");
-      if (t->advect_unfused != 0 && t->advect_unfused != 1) return fail(UF_ERR_ARG, "advect_unfused must be 0 or 1");
+      if (t->unfused & ~(UF_UNFUSED_ADVECT | UF_UNFUSED_MOMENTUM)) return fail(UF_ERR_ARG, "unknown bit in unfused");
     }
     drop_graphs();
     advect_zc_tuned = t ? t->advect_zc : 0;
-    advect_unfused = t ? t->advect_unfused : 0;
+    unfused = t ? t->unfused : 0;
     for (int l = 0; l < uf::MAX_LEVELS; ++l) march_zc_tuned[l] = t ? t->march_zc[l] : 0;
     return set_tail_level(t && t->tail_level > 0 ? t->tail_level : P.auto_tail_level);
   }
@@ -1357,7 +1374,7 @@ class GridImpl final : public uf_grid {
       t.tail_level = c.lt;
       for (int l = 0; l < UF_MAX_LEVELS; ++l) t.march_zc[l] = c.zc;
       t.advect_zc = advect_zc_tuned;       // the solve's candidates keep the step's other knobs
-      t.advect_unfused = advect_unfused;
+      t.unfused = unfused;
       rs = set_tuning(&t);
       if (rs != UF_OK) break;
       cudaGraphExec_t ex = nullptr;

@@ -1,11 +1,13 @@
 """The fused step kernels against the separate sub-step kernels they replace.
 
 The fused MacCormack advection forms every value with the expressions of
-the two-pass form (forward and backward semi-Lagrangian kernels) from the
-same inputs, so whole steps agree bit for bit: in FP32 and FP64, on ragged
-grids, with the CFL time step (displacements below half a cell: everything
-from the staged tiles) and with a fixed time step three times larger
-(displacements past a cell: the global-memory fallbacks)."""
+the two-pass form (forward and backward semi-Lagrangian kernels), and the
+fused diffusion + drag + BC + right-hand-side kernel with those of its
+three kernels (||b||^2 summed in the same order), from the same inputs, so
+whole steps agree bit for bit: in FP32 and FP64, on ragged grids, with the
+CFL time step (displacements below half a cell: everything from the staged
+tiles) and with a fixed time step three times larger (displacements past a
+cell: the global-memory fallbacks); each fusion alone and both together."""
 import numpy as np
 import pytest
 
@@ -27,7 +29,7 @@ def _lib():
 
 def run(sc, precision, unfused, nsteps, **extra):
     g = uf.Grid(sc.nx, sc.ny, sc.nz, precision=precision, **{**sc.params(), **extra})
-    g.set_tuning(advect_unfused=unfused)
+    g.set_tuning(unfused=unfused)
     g.set_porosity(sc.phi.astype(g.np_dtype))
     g.init_state()
     for _ in range(nsteps):
@@ -39,7 +41,8 @@ def run(sc, precision, unfused, nsteps, **extra):
 
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 @pytest.mark.parametrize("dt_scale", [0.0, 3.0])
-def test_fused_advection_equals_two_pass_bitwise(precision, dt_scale):
+@pytest.mark.parametrize("unfused", [uf.UNFUSED_ADVECT, uf.UNFUSED_MOMENTUM, uf.UNFUSED_ALL])
+def test_fused_step_equals_sub_step_kernels_bitwise(precision, dt_scale, unfused):
     sc = layouts.urban_block(45, 37, 19, h=2.0, seed=3, wind_dir_deg=135.0)
     extra = {}
     if dt_scale > 0:
@@ -49,8 +52,8 @@ def test_fused_advection_equals_two_pass_bitwise(precision, dt_scale):
         dt = probe.step().dt
         probe.close()
         extra["fixed_dt"] = dt_scale * dt
-    a = run(sc, precision, False, 3, **extra)
-    b = run(sc, precision, True, 3, **extra)
+    a = run(sc, precision, 0, 3, **extra)
+    b = run(sc, precision, unfused, 3, **extra)
     for n in NAMES:
         assert np.array_equal(a[n], b[n]), n
 
@@ -59,10 +62,21 @@ def test_fused_advection_tuning_roundtrip():
     g = uf.Grid(40, 24, 18, precision="f32")
     g.set_tuning(advect_zc=5)
     t, _ = g.get_tuning()
-    assert t["advect_zc"] == 5 and t["advect_unfused"] == 0
+    assert t["advect_zc"] == 5 and t["unfused"] == 0
     g.set_tuning()
     t, _ = g.get_tuning()
     assert t["advect_zc"] == 16
     with pytest.raises(uf.UFError):
         g.set_tuning(advect_zc=65)
     g.close()
+
+
+def test_fused_step_with_the_paper_preconditioner():
+    """A grid with the approximate-inverse preconditioner (no multigrid
+    tail) runs the same fused kernels, and they agree with the sub-step
+    kernels bit for bit there too."""
+    sc = layouts.urban_block(40, 32, 12, h=2.0, seed=5)
+    a = run(sc, "f32", 0, 2, precond="ai1", cg_max_iter=2000)
+    b = run(sc, "f32", uf.UNFUSED_ALL, 2, precond="ai1", cg_max_iter=2000)
+    for n in NAMES:
+        assert np.array_equal(a[n], b[n]), n
