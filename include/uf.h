@@ -168,6 +168,23 @@ uf_status uf_get_state(uf_grid* g, int field, void* buf);
 uf_status uf_set_fields(uf_grid* g, int n, const int* fields, const void* const* bufs);
 uf_status uf_get_fields(uf_grid* g, int n, const int* fields, void* const* bufs);
 
+/* Snapshot of the complete time-stepping state, for checkpoint and resume
+ * (the paper has no counterpart).  Besides the fields uf_set_fields
+ * writes, the time integration carries the pressure history: each step's
+ * solve starts from the guess 2 p^n - p^{n-1}, and the pressure is held in
+ * twice the working precision.  uf_set_fields cannot restore either, so a
+ * run restarted from its fields takes a different (equally converged) CG
+ * path.  uf_save_state copies the face velocities, k, omega, p^n and the
+ * next guess (both in the pressure store) into a caller-owned device
+ * buffer of uf_state_bytes(g) bytes; uf_load_state puts them back, after
+ * which the steps reproduce the uninterrupted run bit for bit.  The layout
+ * is private to the grid's size and precision.  Both are asynchronous on
+ * the grid's stream; UF_ERR_NOMEM if the buffer is smaller than
+ * uf_state_bytes, UF_ERR_STATE if there is no state to save. */
+size_t uf_state_bytes(uf_grid* g);
+uf_status uf_save_state(uf_grid* g, void* d_buf, size_t bytes);
+uf_status uf_load_state(uf_grid* g, const void* d_buf, size_t bytes);
+
 /* Initial state: the inflow profile on every face (Dirichlet values on the
  * boundary faces), k and omega at the inlet values of Sec. 3
  * (k = 1.5 (I U)^2, omega = k^1/2 / (C_mu^1/4 L)), one drag step with the

@@ -1430,6 +1430,27 @@ class GridImpl final : public uf_grid {
   void advanced(int nsteps) override { parity ^= (nsteps & 1); }
   uf_status read_status(uf_step_stats* out) override { return check_device(out); }
 
+  // Checkpoint / resume: the adjoint's checkpoint layout (faces, k, omega,
+  // p^n and the next guess in the pressure store), 256-byte aligned inside
+  // the caller's buffer.
+  size_t state_bytes() override { return adj_layout(1, 1).ckpt * sizeof(T) + 256; }
+  uf_status save_snapshot(void* buf, size_t bytes) override {
+    if (!buf) return fail(UF_ERR_ARG, "NULL state buffer");
+    if (bytes < state_bytes()) return fail(UF_ERR_NOMEM, "state buffer smaller than uf_state_bytes()");
+    if (!have_state) return fail(UF_ERR_STATE, "no state: call uf_init_state or uf_set_state first");
+    T* slot = reinterpret_cast<T*>(round_up(reinterpret_cast<size_t>(buf), 256));
+    UF_CUDA(save_state(slot, adj_layout(1, 1)));
+    return UF_OK;
+  }
+  uf_status load_snapshot(const void* buf, size_t bytes) override {
+    if (!buf) return fail(UF_ERR_ARG, "NULL state buffer");
+    if (bytes < state_bytes()) return fail(UF_ERR_NOMEM, "state buffer smaller than uf_state_bytes()");
+    const T* slot = reinterpret_cast<const T*>(round_up(reinterpret_cast<size_t>(buf), 256));
+    UF_CUDA(load_state(slot, adj_layout(1, 1)));
+    have_state = true;
+    return UF_OK;
+  }
+
   void fill_view(void* vp) override {
     GridView<T>& V = *reinterpret_cast<GridView<T>*>(vp);
     std::memset(&V, 0, sizeof(V));
@@ -2236,6 +2257,9 @@ uf_status uf_set_fields(uf_grid* g, int n, const int* fields, const void* const*
   UF_NEED(g);
   return g->set_fields(n, fields, bufs);
 }
+size_t uf_state_bytes(uf_grid* g) { return g ? g->state_bytes() : 0; }
+uf_status uf_save_state(uf_grid* g, void* buf, size_t bytes) { UF_NEED(g); return g->save_snapshot(buf, bytes); }
+uf_status uf_load_state(uf_grid* g, const void* buf, size_t bytes) { UF_NEED(g); return g->load_snapshot(buf, bytes); }
 uf_status uf_get_fields(uf_grid* g, int n, const int* fields, void* const* bufs) {
   UF_NEED(g);
   return g->get_fields(n, fields, bufs);

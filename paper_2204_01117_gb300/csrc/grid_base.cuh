@@ -72,4 +72,8 @@ struct uf_grid {
   virtual void fill_view(void* view) = 0;          // GridView<T>* of the grid's precision
   virtual void advanced(int nsteps) = 0;           // the state was stepped nsteps times by a batch
   virtual uf_status read_status(uf_step_stats*) = 0;
+  // checkpoint / resume
+  virtual size_t state_bytes() = 0;
+  virtual uf_status save_snapshot(void*, size_t) = 0;
+  virtual uf_status load_snapshot(const void*, size_t) = 0;
 };

@@ -203,6 +203,12 @@ def load():
     lib.uf_set_fields.restype = ip
     lib.uf_get_fields.argtypes = [vp, ip, P(ip), P(vp)]
     lib.uf_get_fields.restype = ip
+    lib.uf_state_bytes.argtypes = [vp]
+    lib.uf_state_bytes.restype = ctypes.c_size_t
+    lib.uf_save_state.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.uf_save_state.restype = ip
+    lib.uf_load_state.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.uf_load_state.restype = ip
     lib.uf_objective_ex.argtypes = [vp, P(ObjectiveDesc), P(dp)]
     lib.uf_objective_ex.restype = ip
     lib.uf_adjoint_run_ex.argtypes = [vp, vp, ctypes.c_size_t, ip, ip, P(ObjectiveDesc), vp, P(dp)]
@@ -706,6 +712,22 @@ class Grid:
     def set_fields(self, st: dict) -> None:
         for n, val in st.items():
             self.set_state(n, val if _is_tensor(val) else np.asarray(val, dtype=self.np_dtype))
+
+    # -- checkpoint / resume ------------------------------------------------
+    def save_checkpoint(self, out=None):
+        """uf_save_state into a CUDA uint8 tensor (new, or `out`): the whole
+        time-stepping state, pressure history included."""
+        import torch
+        n = int(self.lib.uf_state_bytes(self._h))
+        buf = out if out is not None else torch.empty(n, dtype=torch.uint8, device="cuda")
+        if not (buf.is_cuda and buf.dtype == torch.uint8 and buf.numel() >= n):
+            raise TypeError(f"checkpoint buffer must be a CUDA uint8 tensor of >= {n} bytes")
+        check(self.lib.uf_save_state(self._h, ctypes.c_void_p(buf.data_ptr()), buf.numel()))
+        return buf
+
+    def load_checkpoint(self, buf) -> None:
+        """uf_load_state from a tensor written by save_checkpoint."""
+        check(self.lib.uf_load_state(self._h, ctypes.c_void_p(buf.data_ptr()), buf.numel()))
 
 
 class Batch:

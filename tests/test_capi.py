@@ -118,3 +118,8 @@ def test_paper_stop_rule_needs_a_simple_preconditioner(lib):
     assert "App. A.3" in uf.last_error()
     assert uf.workspace_bytes(uf.default_desc(precond="ai2", cg_stop_rule="paper")) > 0
     assert uf.workspace_bytes(uf.default_desc(cg_stop_rule=2)) == 0
+
+
+def test_checkpoint_calls_declared():
+    for name in ("uf_state_bytes", "uf_save_state", "uf_load_state"):
+        assert name in uf.declared_functions()
