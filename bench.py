@@ -190,15 +190,33 @@ def ncu_traffic(kernel_label: str):
     return None
 
 
-def step_traffic(kernels: dict, ms_per_step: float, peak: float, cells: int) -> dict:
-    """Algorithmic bytes of one whole step -- the sum over an eagerly
-    launched step of each kernel's bytes per launch times its launches --
-    and their rate over the graph-replayed step time, against the HBM peak.
+def step_traffic(kernels: dict, prof_iters: int, mean_iters: float, ms_per_step: float, peak: float,
+                 cells: int) -> dict:
+    """Algorithmic bytes of one whole step and their rate over the
+    graph-replayed step time, against the HBM peak.
+
+    One counting, per kernel: its bytes per launch (the compulsory reads and
+    writes of the launch, from uf_profile_step) times its launches per step.
+    The eagerly profiled step ran prof_iters CG iterations; a kernel that
+    launched at least that many times runs once per iteration (plus a fixed
+    number of set-up launches), the others a fixed number of times per step.
+    The per-iteration launches are then taken at mean_iters, the mean CG
+    iterations of the timed steps, so bytes and time describe the same steps.
     Never raises: a malformed profile gives {"error": ...}."""
     try:
-        b = float(sum(k["bytes_per_launch"] * k["launches"] for k in kernels.values()))
-        gbs = b / (ms_per_step * 1e-3) / 1e9
-        return {"bytes": b, "bytes_per_cell": b / cells, "achieved": gbs, "unit": "GB/s", "frac": gbs / peak}
+        fixed = per_iter = 0.0
+        for k in kernels.values():
+            n, b = int(k["launches"]), float(k["bytes_per_launch"])
+            if prof_iters > 0 and n >= prof_iters:
+                fixed += b * (n - prof_iters)
+                per_iter += b
+            else:
+                fixed += b * n
+        total = fixed + per_iter * mean_iters
+        gbs = total / (ms_per_step * 1e-3) / 1e9
+        return {"bytes": total, "bytes_per_cell": total / cells, "fixed_bytes_per_cell": fixed / cells,
+                "per_cg_iteration_bytes_per_cell": per_iter / cells, "cg_iters_mean": mean_iters,
+                "achieved": gbs, "unit": "GB/s", "frac": gbs / peak}
     except Exception as e:   # noqa: BLE001 -- a report field, not a reason to lose the bench line
         return {"error": repr(e)}
 
@@ -895,7 +913,8 @@ def run_ours(args):
                      "peak_source": f"hbm_gbs of {peak_kind}",
                      "kernel_share_of_step": dom["total_ms"] / total_prof,
                      "bytes_per_launch": dom["bytes_per_launch"], "avg_launch_us": avg_ms * 1e3,
-                     "step": step_traffic(kernels, ms / args.steps, peak, sc.cells)},
+                     "step": step_traffic(kernels, pst.cg_iters, iters_timed / args.steps, ms / args.steps, peak,
+                                          sc.cells)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
         "gpu_launches": int(launches),

@@ -7,16 +7,20 @@ import bench
 
 
 def test_step_traffic_sums_bytes_times_launches():
-    kernels = {"a": {"bytes_per_launch": 100.0, "launches": 3, "total_ms": 1.0},
-               "b": {"bytes_per_launch": 50.0, "launches": 2, "total_ms": 1.0}}
-    r = bench.step_traffic(kernels, ms_per_step=1e-3, peak=1.0, cells=4)     # 400 B in 1 us
-    assert r["bytes"] == 400.0 and r["bytes_per_cell"] == 100.0
-    assert r["achieved"] == pytest.approx(400.0 / 1e-6 / 1e9) and r["frac"] == pytest.approx(r["achieved"])
+    # profiled step with 4 CG iterations: "cg" ran once per iteration, "pre"
+    # once per iteration plus one set-up launch, "fix" twice per step
+    kernels = {"cg": {"bytes_per_launch": 10.0, "launches": 4}, "pre": {"bytes_per_launch": 1.0, "launches": 5},
+               "fix": {"bytes_per_launch": 100.0, "launches": 2}}
+    r = bench.step_traffic(kernels, prof_iters=4, mean_iters=2.5, ms_per_step=1e-3, peak=1.0, cells=4)
+    fixed, per_iter = 1.0 + 200.0, 11.0
+    assert r["fixed_bytes_per_cell"] == fixed / 4 and r["per_cg_iteration_bytes_per_cell"] == per_iter / 4
+    assert r["bytes"] == fixed + 2.5 * per_iter
+    assert r["achieved"] == (fixed + 2.5 * per_iter) / 1e-6 / 1e9
 
 
 def test_step_traffic_never_raises():
-    assert "error" in bench.step_traffic({"a": {}}, 1.0, 1.0, 1)
-    assert "error" in bench.step_traffic({"a": {"bytes_per_launch": 1.0, "launches": 1}}, 0.0, 1.0, 1)
+    assert "error" in bench.step_traffic({"a": {}}, 1, 1.0, 1.0, 1.0, 1)
+    assert "error" in bench.step_traffic({"a": {"bytes_per_launch": 1.0, "launches": 1}}, 1, 1.0, 0.0, 1.0, 1)
 
 
 def test_digest_covers_the_profiled_kernel_headers():
