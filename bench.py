@@ -388,6 +388,14 @@ def batched_leg(steps: int = 10, peak: float = 6790.0, peak_kind: str = "measure
     st = b.run(1)
     fixed, per_iter = b.launch_counts()
     prof = b.profile_step()
+    inst_cells = [sc.nx * sc.ny * sc.nz for sc in insts]
+    # whole batched step with the single-grid counting: the CG-loop launches of
+    # the profiled step ran as often as its slowest instance needed (the others
+    # skip their items), so they are taken at the cell-weighted mean of the
+    # instances' own iteration counts
+    prof_iters = int(prof.get("b_cg_dir_q", {}).get("launches", 0))
+    mean_iters = sum(c * x.cg_iters for c, x in zip(inst_cells, st)) / float(sum(inst_cells))
+    step_bytes = step_traffic(prof, prof_iters, mean_iters, ms_b / steps, peak, cells)
     dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
     avg_ms = dom["total_ms"] / dom["launches"]
     achieved = dom["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
@@ -428,6 +436,7 @@ def batched_leg(steps: int = 10, peak: float = 6790.0, peak_kind: str = "measure
         "speedup": ms_s / ms_b,
         "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
+                     "step": step_bytes,
                      "kernel_share_of_step": dom["total_ms"] / total_prof,
                      "bytes_per_launch": dom["bytes_per_launch"], "avg_launch_us": avg_ms * 1e3},
     }

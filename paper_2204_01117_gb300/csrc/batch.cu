@@ -67,7 +67,7 @@ struct LaunchMap {
 };
 
 // Launch kinds: one work list each (march levels: one per level).
-enum MapKind { MAP_CFL = 0, MAP_CELL, MAP_FACE, MAP_CHUNK, MAP_TAIL, MAP_MARCH0 };
+enum MapKind { MAP_CFL = 0, MAP_CELL, MAP_FACE, MAP_CHUNK, MAP_TAIL, MAP_ADV, MAP_MARCH0 };
 constexpr int kMaps = MAP_MARCH0 + uf::MAX_LEVELS;
 
 __device__ __forceinline__ int map_entry(const LaunchMap* __restrict__ m, int w) {
@@ -152,10 +152,8 @@ struct AdvP {
   uf::AdvectArgs<T> a;
 };
 template <typename T>
-struct FaceP {   // diffusion (c = nu_t), drag + BCs (c = drag coefficient)
-  uf::StepParams<T> sp;
-  const T *ui, *vi, *wi, *c;
-  T *uo, *vo, *wo;
+struct MomP {    // fused diffusion + drag + BCs + pressure right-hand side
+  uf::MomentumArgs<T> M;
 };
 template <typename T>
 struct ProjP {   // projection from the pressure store
@@ -169,14 +167,6 @@ struct CommitP { // p^{n+1} from the solve's correction, in the pressure store
   T* delta;
   uf::PStore<T> *pn, *gs;
   const uf::SolveState* st;
-};
-template <typename T>
-struct RhsP {
-  uf::StepParams<T> sp;
-  const T *u, *v, *w;
-  T* b;
-  double* partials;
-  uf::SolveState* st;
 };
 template <typename T>
 struct CgP {     // CG initial residual, direction + A d
@@ -224,37 +214,13 @@ __global__ void __launch_bounds__(uf::NT, 6) kb_eddy(const __grid_constant__ Arg
 }
 
 template <typename T>
-__global__ void __launch_bounds__(uf::NT, 6) kb_advect_forward(const __grid_constant__ Args<AdvP<T>> A) {
-  for_plane_items(&A.m, [&](int i, const VBlock& vb) { uf::advect_forward_body<T>(A.at[i].a, vb); });
+__global__ void __launch_bounds__(uf::MT, UF_ADVECT_MINB) kb_advect_fused(const __grid_constant__ Args<AdvP<T>> A) {
+  for_items(&A.m, [&](int i, int zc, const VBlock& vb) { uf::advect_fused_body<T>(A.at[i].a, zc, vb); });
 }
 
 template <typename T>
-__global__ void __launch_bounds__(uf::NT, 6) kb_advect_backward(const __grid_constant__ Args<AdvP<T>> A) {
-  for_plane_items(&A.m, [&](int i, const VBlock& vb) { uf::advect_backward_body<T>(A.at[i].a, vb); });
-}
-
-template <typename T>
-__global__ void __launch_bounds__(uf::NT, 6) kb_diffuse(const __grid_constant__ Args<FaceP<T>> A) {
-  for_plane_items(&A.m, [&](int i, const VBlock& vb) {
-    const FaceP<T>& P = A.at[i];
-    uf::diffuse_body<T>(P.sp, P.ui, P.vi, P.wi, P.c, P.uo, P.vo, P.wo, vb);
-  });
-}
-
-template <typename T>
-__global__ void __launch_bounds__(uf::NT, 6) kb_drag_bc(const __grid_constant__ Args<FaceP<T>> A) {
-  for_plane_items(&A.m, [&](int i, const VBlock& vb) {
-    const FaceP<T>& P = A.at[i];
-    uf::drag_bc_body<T>(P.sp, P.ui, P.vi, P.wi, P.c, P.uo, P.vo, P.wo, vb);
-  });
-}
-
-template <typename T>
-__global__ void __launch_bounds__(uf::NT, 6) kb_pressure_rhs(const __grid_constant__ Args<RhsP<T>> A) {
-  for_items(&A.m, [&](int i, int zc, const VBlock& vb) {
-    const RhsP<T>& P = A.at[i];
-    uf::pressure_rhs_body<T>(P.sp, P.u, P.v, P.w, P.b, zc, P.partials, P.st, vb);
-  });
+__global__ void __launch_bounds__(uf::MT) kb_momentum_fused(const __grid_constant__ Args<MomP<T>> A) {
+  for_items(&A.m, [&](int i, int, const VBlock& vb) { uf::momentum_fused_body<T>(A.at[i].M, vb); });
 }
 
 // Opens the batch's CG loop: every instance that takes part is unfinished.
@@ -455,6 +421,7 @@ class BatchImpl final : public uf_batch {
       add_plane_entry(maps[MAP_FACE], i, (d.nx + 1 + uf::BX - 1) / uf::BX, (d.ny + 1 + uf::BY - 1) / uf::BY,
                       3 * d.nz + 1);
       add_entry(maps[MAP_CHUNK], i, G.chunk_g[0], G.chunk_g[1], G.chunk_g[2], G.chunk_zc);
+      add_entry(maps[MAP_ADV], i, G.adv_g[0], G.adv_g[1], G.adv_g[2], G.adv_zc);
       add_entry(maps[MAP_TAIL], i, 1, 1, 1, 0);
       for (int l = 0; l < G.tail_level; ++l)
         add_entry(maps[MAP_MARCH0 + l], i, G.march_g[l][0], G.march_g[l][1], G.march_g[l][2], G.march_zc[l]);
@@ -620,15 +587,6 @@ class BatchImpl final : public uf_batch {
     P.kb[0] = G.kb[0]; P.kb[1] = G.kb[1]; P.ob[0] = G.ob[0]; P.ob[1] = G.ob[1];
     return P;
   }
-  static FaceP<T> face_params(const View<T>& G, const T* ui, const T* vi, const T* wi, const T* c, T* uo, T* vo,
-                              T* wo) {
-    FaceP<T> P;
-    std::memset(&P, 0, sizeof(P));
-    P.sp = G.sp;
-    P.ui = ui; P.vi = vi; P.wi = wi; P.c = c;
-    P.uo = uo; P.vo = vo; P.wo = wo;
-    return P;
-  }
   static CgP<T> cg_params(const View<T>& G) {
     CgP<T> P;
     std::memset(&P, 0, sizeof(P));
@@ -669,28 +627,31 @@ class BatchImpl final : public uf_batch {
       L(s, "b_eddy_viscosity", plane_bytes(MAP_CELL, 6),
         [&] { k<<<grid_of(k, uf::NT, 0, items(MAP_CELL)), blk, 0, s>>>(A, d_par); });
     }
-    {
-      const auto& A = args<AdvP<T>>(MAP_FACE, [](AdvP<T>& P, const View<T>& G) { P.a = G.adv; });
-      launch_plane(kb_advect_forward<T>, MAP_FACE, s, "b_advect_forward", 6, A);
-      launch_plane(kb_advect_backward<T>, MAP_FACE, s, "b_advect_backward", 9, A);
-    }
-    launch_plane(kb_diffuse<T>, MAP_FACE, s, "b_diffuse", 7, args<FaceP<T>>(MAP_FACE, [](FaceP<T>& P, const View<T>& G) {
-      P = face_params(G, G.ut, G.vt, G.wt, G.nut, G.u2, G.v2, G.w2);
-    }));
-    launch_plane(kb_drag_bc<T>, MAP_FACE, s, "b_drag_bc", 7, args<FaceP<T>>(MAP_FACE, [](FaceP<T>& P, const View<T>& G) {
-      P = face_params(G, G.u2, G.v2, G.w2, G.cc, G.u, G.v, G.w);
-    }));
-    {
-      auto k = kb_pressure_rhs<T>;
-      const auto& A = args<RhsP<T>>(MAP_CHUNK, [](RhsP<T>& P, const View<T>& G) {
-        P.sp = G.sp;
-        P.u = G.u; P.v = G.v; P.w = G.w;
-        P.b = G.b;
-        P.partials = G.partials;
-        P.st = G.st;
+    {   // both MacCormack passes (the fused kernel of the single grids, bit for bit the two-pass form)
+      auto k = kb_advect_fused<T>;
+      const auto& A = args<AdvP<T>>(MAP_ADV, [](AdvP<T>& P, const View<T>& G) {
+        P.a = G.adv;
+        P.a.uh = P.a.vh = P.a.wh = nullptr;   // no tape
       });
-      L(s, "b_pressure_rhs", plane_bytes(MAP_CHUNK, 4),
-        [&] { k<<<grid_of(k, uf::NT, 0, items(MAP_CHUNK)), blk, 0, s>>>(A); });
+      const size_t sm = uf::advect_fused_smem_total<T>();
+      L(s, "b_advect_fused", plane_bytes(MAP_ADV, 6),
+        [&] { k<<<grid_of(k, uf::MT, sm, items(MAP_ADV)), uf::MT, sm, s>>>(A); });
+    }
+    {   // diffusion, drag, velocity BCs and the pressure right-hand side in one pass
+      auto k = kb_momentum_fused<T>;
+      const auto& A = args<MomP<T>>(MAP_CHUNK, [](MomP<T>& P, const View<T>& G) {
+        uf::MomentumArgs<T>& M = P.M;
+        M.p = G.sp;
+        M.ut = G.ut; M.vt = G.vt; M.wt = G.wt; M.nut = G.nut; M.cc = G.cc;
+        M.u = G.u; M.v = G.v; M.w = G.w; M.b = G.b;
+        M.u2t = M.v2t = M.w2t = nullptr;
+        M.zc = G.chunk_zc;
+        M.partials = G.partials;
+        M.st = G.st;
+      });
+      const size_t sm = uf::momentum_fused_smem<T>();
+      L(s, "b_momentum_fused", plane_bytes(MAP_CHUNK, 9),
+        [&] { k<<<grid_of(k, uf::MT, sm, items(MAP_CHUNK)), uf::MT, sm, s>>>(A); });
     }
     L(s, "b_begin_solve", 0, [&] { kb_begin_solve<<<1, 32, 0, s>>>(d_left, n); });
     {
@@ -875,6 +836,15 @@ class BatchImpl final : public uf_batch {
       };
       UFB_CUDA(lim((const void*)kb_mg_tail<T, uf::SM_JACOBI>));
       UFB_CUDA(lim((const void*)kb_mg_tail<T, uf::SM_RBGS>));
+      auto lim_static = [&](const void* f) {   // less the kernel's static shared memory
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, f);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+        return e;
+      };
+      UFB_CUDA(lim_static((const void*)kb_advect_fused<T>));
+      UFB_CUDA(lim_static((const void*)kb_momentum_fused<T>));
       UFB_CUDA(cudaStreamSynchronize(stream));
       uf_status s = capture();
       if (s != UF_OK) return s;

@@ -1478,6 +1478,10 @@ class GridImpl final : public uf_grid {
     const dim3 gc = chunk_grid(d.nx, d.ny, d.nz, &zc);
     V.chunk_g[0] = gc.x; V.chunk_g[1] = gc.y; V.chunk_g[2] = gc.z;
     V.chunk_zc = zc;
+    int azc;
+    const dim3 ga = advect_grid(&azc);
+    V.adv_g[0] = ga.x; V.adv_g[1] = ga.y; V.adv_g[2] = ga.z;
+    V.adv_zc = azc;
     V.dt_blocks = kDtBlocks;
     V.st = st;
     V.partials = partials;

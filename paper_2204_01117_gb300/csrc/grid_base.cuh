@@ -6,6 +6,7 @@
 
 #include "../../include/uf.h"
 #include "mg_fused.cuh"
+#include "momentum_fused.cuh"
 
 // Launch geometry and buffers of one grid, as its own graphs use them; the
 // batch replays the same blocks (same z chunks, same tail level), so a grid
@@ -28,7 +29,8 @@ struct GridView {
   size_t tail_smem;
   int march_g[uf::MAX_LEVELS][3];  // blocks of the z-marching level kernels
   int march_zc[uf::MAX_LEVELS];    // z planes per block
-  int chunk_g[3], chunk_zc;        // z-chunked reductions over the cells
+  int chunk_g[3], chunk_zc;        // z-chunked reductions over the cells (and the fused momentum pass)
+  int adv_g[3], adv_zc;            // blocks and z planes per block of the fused advection
   int dt_blocks;                   // blocks of the CFL reduction
   uf::SolveState* st;
   double* partials;
