@@ -407,6 +407,15 @@ typedef struct {
                                  BCs and the pressure right-hand side as
                                  three kernels.  Both forms give the same
                                  values bit for bit.  0 = all fused (default) */
+  int coarse_start;           /* first multigrid level of the V-cycle run as one
+                                 thread-block-cluster launch (down legs, the
+                                 tail, up legs); the levels above it use one
+                                 launch per level and leg.  0 = automatic
+                                 (per-level launches: on the coarse grids
+                                 measured so far the cluster, which holds
+                                 16 SMs at most, is no faster), -1 =
+                                 per-level launches only.  Both give the same
+                                 values bit for bit */
 } uf_tuning;
 
 /* The knobs in use, resolved (no zeros).  levels: number of MG levels. */

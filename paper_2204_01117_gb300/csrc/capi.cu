@@ -21,6 +21,7 @@
 #include "adjoint_kernels.cuh"
 #include "advect_fused.cuh"
 #include "momentum_fused.cuh"
+#include "mg_coarse.cuh"
 #include "mesh_kernels.cuh"
 
 namespace {
@@ -133,7 +134,7 @@ struct Plan {
   size_t tail_smem;        // its dynamic shared memory (bytes)
   size_t tail_cr_off;      // byte offset of the coarsest solve's FP64 right-hand side in it
   std::vector<int> tail_off;
-  std::vector<size_t> lr, lx, lt;
+  std::vector<size_t> lr, lx, lt, lu;   // lu: scratch of the cluster V-cycle (levels >= 1)
   size_t prof, dt, dtT, scal, state, partials, ainv, boxes, grad;
   size_t total;
 };
@@ -165,13 +166,14 @@ Plan make_plan(const uf_grid_desc* d) {
   P.levels = mg_hierarchy(d->nx, d->ny, d->nz, d->mg_coarse_max);
   const bool mg = d->precond == UF_PRECOND_MG;
   const size_t nl = mg ? P.levels.size() : 1;
-  P.lr.assign(nl, 0); P.lx.assign(nl, 0); P.lt.assign(nl, 0);
+  P.lr.assign(nl, 0); P.lx.assign(nl, 0); P.lt.assign(nl, 0); P.lu.assign(nl, 0);
   for (size_t l = 0; l < nl; ++l) {
     const LevelDims& ld = P.levels[l];
     const size_t n = (size_t)ld.P * ld.ny * ld.nz;
     P.lr[l] = l == 0 ? P.r : L.take(n * tb);
     P.lx[l] = L.take(n * tb);
     P.lt[l] = L.take(n * tb);
+    if (l > 0) P.lu[l] = L.take(n * tb);
   }
   const LevelDims& cl = P.levels.back();
   P.coarse_n = mg ? cl.nx * cl.ny * cl.nz : 0;
@@ -341,6 +343,8 @@ class GridImpl final : public uf_grid {
   bool taping = false;
   int unfused = 0;          // tuning: bit mask of fused kernels run as their sub-step kernels
   int advect_zc_tuned = 0;  // tuning: z planes per block of the fused advection (0: automatic)
+  int coarse_start_tuned = 0;  // tuning: first MG level of the cluster V-cycle (0 automatic, -1 off)
+  int cluster_ctas = 0;        // CTAs per cluster of the coarse V-cycle on this device (0: unavailable)
   cudaGraphExec_t init_exec = nullptr, solve_exec = nullptr;
   int parity = 0;
   bool have_state = false;
@@ -458,6 +462,7 @@ class GridImpl final : public uf_grid {
       tail.n_coarse = P.coarse_n;
     }
     UF_CUDA(set_smem_limits());   // every grid: the fused step kernels need more than 48 KB
+    if (d.precond == UF_PRECOND_MG) cluster_ctas = probe_cluster();
     if (d.precond == UF_PRECOND_MG) {
       const LevelDims& cl = P.levels.back();
       const uf::Level<T>& L = lv.back();
@@ -533,6 +538,8 @@ class GridImpl final : public uf_grid {
     lim((const void*)uf::k_mg_tail<T, uf::SM_RBGS>);
     lim((const void*)uf::k_advect_fused<T>);
     lim((const void*)uf::k_momentum_fused<T>);
+    lim((const void*)uf::k_mg_coarse<T, uf::SM_JACOBI>);
+    lim((const void*)uf::k_mg_coarse<T, uf::SM_RBGS>);
     return e;
   }
 
@@ -580,40 +587,116 @@ class GridImpl final : public uf_grid {
     return W;
   }
 
+  // CTAs per cluster for the coarse V-cycle: 16 where the device can
+  // co-schedule such a cluster of 1024-thread CTAs with the tail's shared
+  // memory, else 8, else 0 (per-level kernels only).
+  int probe_cluster() {
+    for (int ctas : {16, 8}) {
+      bool ok = true;
+      for (const void* f : {(const void*)uf::k_mg_coarse<T, uf::SM_JACOBI>, (const void*)uf::k_mg_coarse<T, uf::SM_RBGS>}) {
+        if (ctas > 8 && cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) ok = false;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(ctas, 1, 1);
+        cfg.blockDim = dim3(uf::CT, 1, 1);
+        cfg.dynamicSmemBytes = P.tail_smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = ctas;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (ok && (cudaOccupancyMaxActiveClusters(&nclusters, f, &cfg) != cudaSuccess || nclusters < 1)) ok = false;
+      }
+      cudaGetLastError();   // a refused size is not an error of the grid
+      if (ok) return ctas;
+    }
+    return 0;
+  }
+
+  // First level of the cluster V-cycle (below it, the per-level kernels);
+  // tail_level when the cluster kernel is not used.
+  // Automatic (0) is per-level launches: the cluster runs on 16 SMs at most,
+  // and its phases are slower than the per-level kernels on every level but
+  // the last one or two before the tail, where the two are about even.
+  int coarse_start() const {
+    const int lt = P.tail_level;
+    if (d.precond != UF_PRECOND_MG || cluster_ctas == 0 || coarse_start_tuned <= 0) return lt;
+    return std::min(coarse_start_tuned, lt);
+  }
+
+  // Down kernel of level l (mode 1 on the finest level: with the CG update).
+  template <int SM>
+  void rec_down(cudaStream_t s, int l, int mode, cudaGraphConditionalHandle cond, int use_cond,
+                const uf::SmoothW<T>& om) {
+    const std::string sl = std::to_string(l);
+    int zc;
+    const dim3 g = march_grid(l, &zc);
+    if (l == 0 && mode == 1)
+      L(s, "mg_down_cg_L0", (7 * Nl(0) + Nl(1)) * tb(), [&] {
+        uf::k_mg_down<T, SM, true><<<g, uf::FT, 0, s>>>(lv[0], lv[1], om, zc, sol_x, d0, d1, q, partials, st, cond,
+                                                       use_cond);
+      });
+    else
+      L(s, "mg_down_L" + sl, (2 * Nl(l) + Nl(l + 1)) * tb(), [&] {
+        uf::k_mg_down<T, SM, false><<<g, uf::FT, 0, s>>>(lv[l], lv[l + 1], om, zc, nullptr, nullptr, nullptr,
+                                                        nullptr, partials, st, cond, 0);
+      });
+  }
+  // Up kernel of level l (the finest writes z and forms r.z).
+  template <int SM>
+  void rec_up(cudaStream_t s, int l, int mode, const uf::SmoothW<T>& om) {
+    const std::string sl = std::to_string(l);
+    int zc;
+    const dim3 g = march_grid(l, &zc);
+    if (l == 0)
+      L(s, "mg_up_L0", (3 * Nl(0) + Nl(1)) * tb(), [&] {
+        uf::k_mg_up<T, SM, true><<<g, uf::FT, 0, s>>>(lv[0], lv[1], om, zc, z, mode, partials, st);
+      });
+    else
+      L(s, "mg_up_L" + sl, (3 * Nl(l) + Nl(l + 1)) * tb(), [&] {
+        uf::k_mg_up<T, SM, false><<<g, uf::FT, 0, s>>>(lv[l], lv[l + 1], om, zc, lv[l].t, mode, partials, st);
+      });
+  }
+
   template <int SM>
   void rec_vcycle_sm(cudaStream_t s, int mode, cudaGraphConditionalHandle cond, int use_cond) {
     const uf::SmoothW<T> om = smooth_weights();
     const int lt = P.tail_level;
-    for (int l = 0; l < lt; ++l) {
-      const std::string sl = std::to_string(l);
-      int zc;
-      const dim3 g = march_grid(l, &zc);
-      if (l == 0 && mode == 1)
-        L(s, "mg_down_cg_L0", (7 * Nl(0) + Nl(1)) * tb(), [&] {
-          uf::k_mg_down<T, SM, true><<<g, uf::FT, 0, s>>>(lv[0], lv[1], om, zc, sol_x, d0, d1, q, partials, st, cond,
-                                                         use_cond);
-        });
-      else
-        L(s, "mg_down_L" + sl, (2 * Nl(l) + Nl(l + 1)) * tb(), [&] {
-          uf::k_mg_down<T, SM, false><<<g, uf::FT, 0, s>>>(lv[l], lv[l + 1], om, zc, nullptr, nullptr, nullptr,
-                                                          nullptr, partials, st, cond, 0);
-        });
+    const int cs = coarse_start();
+    for (int l = 0; l < cs; ++l) rec_down<SM>(s, l, mode, cond, use_cond, om);
+    if (cs < lt) {   // levels cs .. lt-1 and the tail in one cluster launch
+      uf::CoarseArgs<T> ca;
+      std::memset(&ca, 0, sizeof(ca));
+      for (size_t l = 0; l < lv.size(); ++l) {
+        ca.lv[l] = lv[l];
+        ca.lu[l] = l > 0 ? at<T>(P.lu[l]) : nullptr;
+      }
+      ca.cs = cs;
+      ca.lt = lt;
+      double bytes = (double)P.coarse_n * P.coarse_n * 8 + 2 * Nl(lt) * tb();
+      for (int l = cs; l < lt; ++l) bytes += (5 * Nl(l) + 2 * Nl(l + 1)) * tb();
+      L(s, "mg_coarse", bytes, [&] {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cluster_ctas, 1, 1);
+        cfg.blockDim = dim3(uf::CT, 1, 1);
+        cfg.dynamicSmemBytes = P.tail_smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cluster_ctas;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, uf::k_mg_coarse<T, SM>, ca, tail, om, (const uf::SolveState*)st);
+      });
+    } else {
+      L(s, "mg_tail", (double)P.coarse_n * P.coarse_n * 8 + 2 * Nl(lt) * tb(),
+        [&] { uf::k_mg_tail<T, SM><<<1, uf::TAIL_T, P.tail_smem, s>>>(tail, om, st); });
     }
-    L(s, "mg_tail", (double)P.coarse_n * P.coarse_n * 8 + 2 * Nl(lt) * tb(),
-      [&] { uf::k_mg_tail<T, SM><<<1, uf::TAIL_T, P.tail_smem, s>>>(tail, om, st); });
-    for (int l = lt - 1; l >= 0; --l) {
-      const std::string sl = std::to_string(l);
-      int zc;
-      const dim3 g = march_grid(l, &zc);
-      if (l == 0)
-        L(s, "mg_up_L0", (3 * Nl(0) + Nl(1)) * tb(), [&] {
-          uf::k_mg_up<T, SM, true><<<g, uf::FT, 0, s>>>(lv[0], lv[1], om, zc, z, mode, partials, st);
-        });
-      else
-        L(s, "mg_up_L" + sl, (3 * Nl(l) + Nl(l + 1)) * tb(), [&] {
-          uf::k_mg_up<T, SM, false><<<g, uf::FT, 0, s>>>(lv[l], lv[l + 1], om, zc, lv[l].t, mode, partials, st);
-        });
-    }
+    for (int l = cs - 1; l >= 0; --l) rec_up<SM>(s, l, mode, om);
   }
   void rec_vcycle(cudaStream_t s, int mode, cudaGraphConditionalHandle cond, int use_cond) {
     if (d.mg_smoother == UF_SMOOTH_RBGS) rec_vcycle_sm<uf::SM_RBGS>(s, mode, cond, use_cond);
@@ -1320,6 +1403,7 @@ class GridImpl final : public uf_grid {
     advect_grid(&azc);
     t->advect_zc = azc;
     t->unfused = unfused;
+    t->coarse_start = coarse_start() < P.tail_level ? coarse_start() : -1;
     if (levels) *levels = P.nl;
     return UF_OK;
   }
@@ -1332,16 +1416,20 @@ class GridImpl final : public uf_grid {
       }
       if (t->advect_zc < 0 || t->advect_zc > 64) return fail(UF_ERR_ARG, "advect_zc must be in [0, 64]");
       if (t->unfused & ~(UF_UNFUSED_ADVECT | UF_UNFUSED_MOMENTUM)) return fail(UF_ERR_ARG, "unknown bit in unfused");
+      if (t->coarse_start < -1 || t->coarse_start >= UF_MAX_LEVELS) return fail(UF_ERR_ARG, "coarse_start out of range");
     }
     drop_graphs();
     advect_zc_tuned = t ? t->advect_zc : 0;
     unfused = t ? t->unfused : 0;
+    coarse_start_tuned = t ? t->coarse_start : 0;
     for (int l = 0; l < uf::MAX_LEVELS; ++l) march_zc_tuned[l] = t ? t->march_zc[l] : 0;
     return set_tail_level(t && t->tail_level > 0 ? t->tail_level : P.auto_tail_level);
   }
 
   // Autotuner: candidates = tail level (automatic and up to two levels
-  // deeper) x a uniform tile depth (automatic, 2, 4, 8); each is timed over
+  // deeper) x a uniform tile depth (automatic, 2, 4, 8) x per-level launches
+  // or the cluster V-cycle over the last level above the tail (where the
+  // device co-schedules the cluster); each is timed over
   // `reps` solves of a synthetic right-hand side from a zero guess, with the
   // unknown and the right-hand side in scratch buffers (ut, uh) that no step
   // keeps between steps.
@@ -1360,11 +1448,15 @@ class GridImpl final : public uf_grid {
     UF_CUDA(cudaEventCreate(&e0));
     UF_CUDA(cudaEventCreate(&e1));
     struct Cand {
-      int lt, zc;
+      int lt, zc, cs;
     };
     std::vector<Cand> cands;
     for (int lt = P.auto_tail_level; lt <= std::min(P.nl - 1, P.auto_tail_level + 2); ++lt)
-      for (int zc : {0, 2, 4, 8}) cands.push_back({lt, zc});
+      for (int zc : {0, 2, 4, 8}) {
+        cands.push_back({lt, zc, -1});
+        // the cluster V-cycle over the last level before the tail
+        if (d.precond == UF_PRECOND_MG && cluster_ctas > 0 && lt >= 2) cands.push_back({lt, zc, lt - 1});
+      }
     double best = 1e300;
     uf_tuning best_t;
     uf_status rs = UF_OK;
@@ -1375,6 +1467,7 @@ class GridImpl final : public uf_grid {
       for (int l = 0; l < UF_MAX_LEVELS; ++l) t.march_zc[l] = c.zc;
       t.advect_zc = advect_zc_tuned;       // the solve's candidates keep the step's other knobs
       t.unfused = unfused;
+      t.coarse_start = c.cs;
       rs = set_tuning(&t);
       if (rs != UF_OK) break;
       cudaGraphExec_t ex = nullptr;

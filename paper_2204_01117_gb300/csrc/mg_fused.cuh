@@ -137,19 +137,42 @@ __device__ __forceinline__ float rdiag(float D) {
 }
 __device__ __forceinline__ double rdiag(double D) { return 1.0 / D; }
 
+// Arithmetic with every operation rounded as written (the compiler fuses no
+// multiply into an add on its own): the smoother and residual expressions
+// below are shared by the per-level kernels and the cluster V-cycle, and
+// this way both compute them alike, bit for bit.
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// w_x (a1 + a2) + w_y (b1 + b2) + w_z (c1 + c2): the weighted sum of the six
+// neighbours of a cell (x pair, y pair, z pair).
+template <typename T>
+__device__ __forceinline__ T nb6(T wx, T a1, T a2, T wy, T b1, T b2, T wz, T c1, T c2) {
+  return fma_rn(wz, add_rn(c1, c2), fma_rn(wy, add_rn(b1, b2), mul_rn(wx, add_rn(a1, a2))));
+}
+// Residual r - A x at a cell, with q = r/D: D (q - x) + sum_6 w x_nb.
+template <typename T>
+__device__ __forceinline__ T resid(T D, T q, T x, T nbsum) {
+  return fma_rn(D, add_rn(q, -x), nbsum);
+}
+
 // Pre-smoothing from zero with q = r/D staged: weighted Jacobi x2 = pa q_c +
 // pb/D_c sum w_a q_nb;  RBGS red q_c, black q_c + sum w_a q_nb / D_c.
 template <int SM, typename T>
 __device__ __forceinline__ T presmooth(T qc, T s, T D, const SmoothW<T>& W, bool red) {
-  if (SM == SM_JACOBI) return W.pa * qc + W.pb * s * rdiag(D);
-  return red ? qc : qc + s * rdiag(D);
+  if (SM == SM_JACOBI) return fma_rn(W.pa, qc, mul_rn(mul_rn(W.pb, s), rdiag(D)));
+  return red ? qc : fma_rn(s, rdiag(D), qc);
 }
 // Post-smoothing pass on t: weighted Jacobi t + w (r - D t + s)/D; RBGS
 // relaxes the colour `relax` and keeps the other.
 template <int SM, typename T>
 __device__ __forceinline__ T relax(T tc, T rc, T s, T D, T omega, bool active) {
-  if (SM == SM_JACOBI) return tc + omega * (rc - D * tc + s) * rdiag(D);
-  return active ? (rc + s) * rdiag(D) : tc;
+  if (SM == SM_JACOBI) return fma_rn(mul_rn(omega, add_rn(fma_rn(-D, tc, rc), s)), rdiag(D), tc);
+  return active ? mul_rn(add_rn(rc, s), rdiag(D)) : tc;
 }
 
 // ------------------------------------------------------------ down -------
@@ -254,7 +277,7 @@ __device__ __forceinline__ void mg_down_body(const Level<T>& F, const Level<T>& 
       T v = 0;
       if (kin && px[h].ok) {
         const int b = sxq[h];
-        const T s = F.wx * (qc[b - 1] + qc[b + 1]) + F.wy * (qc[b - QX] + qc[b + QX]) + F.wz * (qm[b] + qp[b]);
+        const T s = nb6(F.wx, qc[b - 1], qc[b + 1], F.wy, qc[b - QX], qc[b + QX], F.wz, qm[b], qp[b]);
         v = presmooth<SM>(qc[b], s, px[h].dxy + dz, W, ((par[h] + k) & 1) == 0);
       }
       dst[sx[h]] = v;
@@ -306,8 +329,8 @@ __device__ __forceinline__ void mg_down_body(const Level<T>& F, const Level<T>& 
       const T* xp = sX[xs_p];
       const T xv = xc[b1];
       F.x[oc] = xv;
-      res = (po.dxy + diag_z(F, k)) * (sQ[ring4(k)][b2] - xv) + F.wx * (xc[b1 - 1] + xc[b1 + 1]) +
-            F.wy * (xc[b1 - XX] + xc[b1 + XX]) + F.wz * (xm[b1] + xp[b1]);
+      res = resid(po.dxy + diag_z(F, k), sQ[ring4(k)][b2], xv,
+                  nb6(F.wx, xc[b1 - 1], xc[b1 + 1], F.wy, xc[b1 - XX], xc[b1 + XX], F.wz, xm[b1], xp[b1]));
       if (CG) {
         const T rv = o_r - alpha * o_q;
         r_out[oc] = rv;
@@ -456,7 +479,7 @@ __device__ __forceinline__ void mg_up_body(const Level<T>& F, const Level<T>& C,
       T v = 0;
       if (kin && pu[h].ok) {
         const int b = sut[h];
-        const T s = F.wx * (tc[b - 1] + tc[b + 1]) + F.wy * (tc[b - QX] + tc[b + QX]) + F.wz * (tm[b] + tp[b]);
+        const T s = nb6(F.wx, tc[b - 1], tc[b + 1], F.wy, tc[b - QX], tc[b + QX], F.wz, tm[b], tp[b]);
         v = relax<SM>(tc[b], pr[h], s, pu[h].dxy + dz, W.w1, ((par[h] + k) & 1) == 1);
       }
       dst[su[h]] = v;
@@ -495,7 +518,7 @@ __device__ __forceinline__ void mg_up_body(const Level<T>& F, const Level<T>& C,
       const T* um = sU[us_m];
       const T* uc = sU[us_c];
       const T* up = sU[us_p];
-      const T s = F.wx * (uc[b - 1] + uc[b + 1]) + F.wy * (uc[b - XX] + uc[b + XX]) + F.wz * (um[b] + up[b]);
+      const T s = nb6(F.wx, uc[b - 1], uc[b + 1], F.wy, uc[b - XX], uc[b + XX], F.wz, um[b], up[b]);
       const T zv = relax<SM>(uc[b], o_r, s, po.dxy + diag_z(F, k), W.w2, ((opar + k) & 1) == 0);
       out[oc] = zv;
       if (FINEST) dacc.add(o_r, zv);

@@ -103,11 +103,11 @@ def objective_desc(objective=None, band=(1.0, 3.0, 4.0, 1.0)):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("tail_level", ctypes.c_int), ("march_zc", ctypes.c_int * MAX_LEVELS),
-                ("advect_zc", ctypes.c_int), ("unfused", ctypes.c_int)]
+                ("advect_zc", ctypes.c_int), ("unfused", ctypes.c_int), ("coarse_start", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {"tail_level": self.tail_level, "march_zc": list(self.march_zc), "advect_zc": self.advect_zc,
-                "unfused": self.unfused}
+                "unfused": self.unfused, "coarse_start": self.coarse_start}
 
 
 class KernelTime(ctypes.Structure):
@@ -649,18 +649,22 @@ class Grid:
         check(self.lib.uf_get_tuning(self._h, ctypes.byref(t), ctypes.byref(n)))
         return t.as_dict(), n.value
 
-    def set_tuning(self, tail_level: int = 0, march_zc=None, advect_zc: int = 0, unfused: int = 0) -> None:
+    def set_tuning(self, tail_level: int = 0, march_zc=None, advect_zc: int = 0, unfused: int = 0,
+                   coarse_start: int = 0) -> None:
         """0 / None: automatic.  march_zc: per-level z planes per block;
         advect_zc: z planes per block of the fused advection; unfused: bit
         mask of fused kernels to run as their separate sub-step kernels
         (1: advection, 2: diffusion + drag + BCs + pressure right-hand side;
-        True: all).  Both forms give the same values."""
+        True: all); coarse_start: first MG level of the one-launch cluster
+        V-cycle (0 automatic = per-level launches, -1 per-level launches).
+        Every choice gives the same values."""
         t = Tuning()
         t.tail_level = tail_level
         for l, z in enumerate(march_zc or []):
             t.march_zc[l] = z
         t.advect_zc = advect_zc
         t.unfused = UNFUSED_ALL if unfused is True else int(unfused)
+        t.coarse_start = int(coarse_start)
         check(self.lib.uf_set_tuning(self._h, ctypes.byref(t)))
 
     def autotune(self, reps: int = 5):

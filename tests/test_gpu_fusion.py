@@ -80,3 +80,28 @@ def test_fused_step_with_the_paper_preconditioner():
     b = run(sc, "f32", uf.UNFUSED_ALL, 2, precond="ai1", cg_max_iter=2000)
     for n in NAMES:
         assert np.array_equal(a[n], b[n]), n
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+@pytest.mark.parametrize("smoother", ["cheby", "rbgs"])
+def test_cluster_vcycle_equals_per_level_kernels_bitwise(precision, smoother):
+    """The coarse levels as one thread-block-cluster launch give the V-cycle
+    of the per-level launches bit for bit, whichever level the cluster
+    starts at."""
+    sc = layouts.urban_block(64, 48, 24, h=2.0, seed=4, wind_dir_deg=250.0)
+    out = {}
+    for cs in (-1, 1, 2):
+        g = uf.Grid(sc.nx, sc.ny, sc.nz, precision=precision, mg_smoother=smoother, **sc.params())
+        g.set_tuning(coarse_start=cs)
+        t, nl = g.get_tuning()
+        if cs > 0:
+            assert t["coarse_start"] in (cs, -1)     # -1: the device cannot co-schedule the cluster
+        g.set_porosity(sc.phi.astype(g.np_dtype))
+        g.init_state()
+        for _ in range(3):
+            g.step()
+        out[cs] = {n: g.get_state(n) for n in NAMES}
+        g.close()
+    for cs in (1, 2):
+        for n in NAMES:
+            assert np.array_equal(out[cs][n], out[-1][n]), (cs, n)
