@@ -85,23 +85,33 @@ def test_fused_step_with_the_paper_preconditioner():
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 @pytest.mark.parametrize("smoother", ["cheby", "rbgs"])
 def test_cluster_vcycle_equals_per_level_kernels_bitwise(precision, smoother):
-    """The coarse levels as one thread-block-cluster launch give the V-cycle
-    of the per-level launches bit for bit, whichever level the cluster
-    starts at."""
-    sc = layouts.urban_block(64, 48, 24, h=2.0, seed=4, wind_dir_deg=250.0)
-    out = {}
-    for cs in (-1, 1, 2):
-        g = uf.Grid(sc.nx, sc.ny, sc.nz, precision=precision, mg_smoother=smoother, **sc.params())
-        g.set_tuning(coarse_start=cs)
-        t, nl = g.get_tuning()
-        if cs > 0:
-            assert t["coarse_start"] in (cs, -1)     # -1: the device cannot co-schedule the cluster
-        g.set_porosity(sc.phi.astype(g.np_dtype))
-        g.init_state()
-        for _ in range(3):
-            g.step()
-        out[cs] = {n: g.get_state(n) for n in NAMES}
-        g.close()
-    for cs in (1, 2):
-        for n in NAMES:
-            assert np.array_equal(out[cs][n], out[-1][n]), (cs, n)
+    """The coarse levels of the V-cycle as per-level launches and as one
+    thread-block-cluster launch from level 1, 2 or 3 down; with the
+    automatic tail and with the tail at the coarsest level (every other
+    level per level).  All give the same three steps bit for bit.  The
+    levels (50 x 42 x 15, 25 x 21 x 8, 13 x 11 x 4, ...) are odd in every
+    axis."""
+    sc = layouts.urban_block(100, 84, 30, h=2.0, seed=4, wind_dir_deg=250.0)
+    variants = {"per level": dict(coarse_start=-1), "cluster 1": dict(coarse_start=1),
+                "cluster 2": dict(coarse_start=2), "cluster 3": dict(coarse_start=3)}
+    for deepest in (False, True):
+        out = {}
+        for name, kw in variants.items():
+            g = uf.Grid(sc.nx, sc.ny, sc.nz, precision=precision, mg_smoother=smoother, **sc.params())
+            nl = g.get_tuning()[1]
+            assert nl >= 5
+            g.set_tuning(tail_level=nl - 1 if deepest else 0, **kw)
+            t = g.get_tuning()[0]
+            assert t["tail_level"] >= 3
+            cs = kw["coarse_start"]
+            if cs > 0 and cs < t["tail_level"]:
+                assert t["coarse_start"] in (cs, -1)   # -1: the device cannot co-schedule the cluster
+            g.set_porosity(sc.phi.astype(g.np_dtype))
+            g.init_state()
+            for _ in range(3):
+                g.step()
+            out[name] = {n: g.get_state(n) for n in NAMES}
+            g.close()
+        for name in variants:
+            for n in NAMES:
+                assert np.array_equal(out[name][n], out["per level"][n]), (deepest, name, n)
