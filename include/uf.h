@@ -103,12 +103,22 @@ typedef struct {
   int mg_coarse_max;       /* coarsest MG level has at most this many cells */
   int mg_smoother;         /* UF_SMOOTH_CHEBY (default), _JACOBI or _RBGS   */
   int cg_stop_rule;        /* UF_STOP_RESIDUAL (default) or UF_STOP_PAPER   */
+  int mg_transfer;         /* UF_TRANSFER_LINEAR (default) or _CONSTANT      */
 } uf_grid_desc;
 
 enum { UF_SMOOTH_JACOBI = 0,   /* damped Jacobi, 2 sweeps before + 2 after        */
        UF_SMOOTH_RBGS = 1,     /* red-black Gauss-Seidel, red-black / black-red   */
        UF_SMOOTH_CHEBY = 2 };  /* 2 weighted-Jacobi sweeps before + 2 after with
                                   the degree-2 Chebyshev weights for [1/3, 2]   */
+
+/* Multigrid transfers between levels.  Between the finest level and level 1
+ * the V-cycle always uses piecewise-constant prolongation and the summed
+ * restriction (its transpose).  LINEAR (default): between coarser levels,
+ * cell-centred linear prolongation (3/4 of the parent, 1/4 of its neighbour
+ * per halved axis; mirrored ghosts at walls, negated at outlets) and its
+ * transpose as the restriction: fewer CG iterations for a little more work
+ * on the small levels.  CONSTANT: piecewise constant on every level. */
+enum { UF_TRANSFER_CONSTANT = 0, UF_TRANSFER_LINEAR = 1 };
 
 typedef struct {
   double dt;               /* time step taken                                */

@@ -255,6 +255,24 @@ __global__ void __launch_bounds__(uf::FT, 4) kb_mg_down(const __grid_constant__ 
   });
 }
 
+// Linear transfers: the right-hand side of level l + 1 from the residual
+// that the down kernel of level l stored (instances without them skip).
+template <typename T>
+__global__ void __launch_bounds__(uf::FT) kb_restrict_lin(const __grid_constant__ Args<MgP<T>> A) {
+  for_items(&A.m, [&](int i, int zc, const VBlock& vb) {
+    const MgP<T>& P = A.at[i];
+    if (P.F.lin) uf::restrict_lin_body<T>(P.F, P.C, zc, P.st, vb);
+  });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(uf::FT) kb_prolong_lin(const __grid_constant__ Args<MgP<T>> A) {
+  for_items(&A.m, [&](int i, int zc, const VBlock& vb) {
+    const MgP<T>& P = A.at[i];
+    if (P.F.lin) uf::prolong_lin_body<T>(P.F, P.C, zc, P.st, vb);
+  });
+}
+
 template <typename T, int SM>
 __global__ void __launch_bounds__(uf::TAIL_T) kb_mg_tail(const View<T>* __restrict__ V,
                                                          const LaunchMap* __restrict__ m) {
@@ -538,8 +556,24 @@ class BatchImpl final : public uf_batch {
         auto k = kb_mg_down<T, SM, false>;
         const auto& A = args<MgP<T>>(kind, [l](MgP<T>& P, const View<T>& G) { P = mg_params(G, l); });
         L(s, "b_mg_down_L" + sl,
-          sum_over(kind, [l](const View<T>& G) { return (2 * cells(G, l) + cells(G, l + 1)) * tb; }),
+          sum_over(kind, [l](const View<T>& G) {
+            return (2 * cells(G, l) + (G.lv[l].lin ? cells(G, l) : cells(G, l + 1))) * tb;
+          }),
           [&] { k<<<grid_of(k, uf::FT, 0, items(kind)), ft, 0, s>>>(A, cond, 0, nullptr); });
+      }
+      // linear transfers: right-hand side of level l + 1 for the instances
+      // that keep it outside their tail
+      if (l + 1 < max_levels) {
+        const int kind1 = MAP_MARCH0 + l + 1;
+        const double bytes = sum_over(kind1, [l](const View<T>& G) {
+          return G.lv[l].lin ? (cells(G, l) + cells(G, l + 1)) * tb : 0.0;
+        });
+        if (bytes > 0) {
+          auto k = kb_restrict_lin<T>;
+          const auto& A = args<MgP<T>>(kind1, [l](MgP<T>& P, const View<T>& G) { P = mg_params(G, l); });
+          L(s, "b_mg_restrict_L" + std::to_string(l + 1), bytes,
+            [&] { k<<<grid_of(k, uf::FT, 0, items(kind1)), ft, 0, s>>>(A); });
+        }
       }
     }
     {
@@ -554,6 +588,20 @@ class BatchImpl final : public uf_batch {
     for (int l = max_levels - 1; l >= 0; --l) {
       const int kind = MAP_MARCH0 + l;
       const std::string sl = std::to_string(l);
+      // linear transfers: the prolonged correction of level l for the
+      // instances whose level l + 1 lies outside their tail (the tail forms
+      // it for the others)
+      if (l + 1 < max_levels) {
+        const int kind1 = MAP_MARCH0 + l + 1;
+        const double pbytes = sum_over(kind1, [l](const View<T>& G) {
+          return G.lv[l].lin ? (cells(G, l) + cells(G, l + 1)) * tb : 0.0;
+        });
+        if (pbytes > 0) {
+          auto k = kb_prolong_lin<T>;
+          const auto& A = args<MgP<T>>(kind1, [l](MgP<T>& P, const View<T>& G) { P = mg_params(G, l); });
+          L(s, "b_mg_prolong_L" + sl, pbytes, [&] { k<<<grid_of(k, uf::FT, 0, items(kind1)), ft, 0, s>>>(A); });
+        }
+      }
       const double bytes = sum_over(kind, [l](const View<T>& G) { return (3 * cells(G, l) + cells(G, l + 1)) * tb; });
       const auto& A = args<MgP<T>>(kind, [l](MgP<T>& P, const View<T>& G) {
         P = mg_params(G, l);

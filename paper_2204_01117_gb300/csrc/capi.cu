@@ -106,6 +106,10 @@ bool desc_valid(const uf_grid_desc* d, std::string* why) {
   if (!(d->ai_omega > 0 && d->ai_omega < 2)) { *why = "ai_omega must lie in (0, 2)"; return false; }
   if (!(d->mg_jacobi_omega > 0 && d->mg_jacobi_omega <= 1)) { *why = "mg_jacobi_omega must lie in (0, 1]"; return false; }
   if (d->mg_coarse_max < 1 || d->mg_coarse_max > 1024) { *why = "mg_coarse_max must lie in [1, 1024]"; return false; }
+  if (d->mg_transfer != UF_TRANSFER_CONSTANT && d->mg_transfer != UF_TRANSFER_LINEAR) {
+    *why = "unknown multigrid transfer";
+    return false;
+  }
   if (!(d->cfl > 0) && !(d->fixed_dt > 0)) { *why = "cfl or fixed_dt must be positive"; return false; }
   // at least one outlet side, otherwise the pressure operator is singular
   const double th = d->wind_dir_deg * M_PI / 180.0;
@@ -449,6 +453,10 @@ class GridImpl final : public uf_grid {
       L.out_mask = out_mask;
       L.r = at<T>(P.lr[l]); L.x = at<T>(P.lx[l]); L.t = at<T>(P.lt[l]);
       L.r_alt = nullptr;
+      // linear transfers below level 1 (the down kernel of such a level
+      // keeps its residual in t, which the up leg overwrites later)
+      L.lin = d.precond == UF_PRECOND_MG && d.mg_transfer == UF_TRANSFER_LINEAR && l >= 1 && l + 1 < nl;
+      L.e = L.lin ? at<T>(P.lu[l]) : nullptr;   // (the cluster V-cycle uses lu only on its own levels)
     }
     if (d.precond == UF_PRECOND_MG) {
       lv[0].r_alt = r2;
@@ -460,6 +468,7 @@ class GridImpl final : public uf_grid {
       tail.nl = (int)nl;
       tail.ainv = ainv;
       tail.n_coarse = P.coarse_n;
+      tail.rin = 0;
     }
     UF_CUDA(set_smem_limits());   // every grid: the fused step kernels need more than 48 KB
     if (d.precond == UF_PRECOND_MG) cluster_ctas = probe_cluster();
@@ -639,15 +648,31 @@ class GridImpl final : public uf_grid {
                                                        use_cond);
       });
     else
-      L(s, "mg_down_L" + sl, (2 * Nl(l) + Nl(l + 1)) * tb(), [&] {
+      L(s, "mg_down_L" + sl, (2 * Nl(l) + (lv[l].lin ? Nl(l) : Nl(l + 1))) * tb(), [&] {
         uf::k_mg_down<T, SM, false><<<g, uf::FT, 0, s>>>(lv[l], lv[l + 1], om, zc, nullptr, nullptr, nullptr,
                                                         nullptr, partials, st, cond, 0);
       });
+    // linear transfers: the right-hand side of level l + 1 from the stored
+    // residual (here also that of the tail's first level: tail.rin = 0)
+    if (lv[l].lin && l + 1 <= P.tail_level) {
+      const unsigned nb = (unsigned)((Nl(l + 1) + uf::FT - 1) / uf::FT);
+      L(s, "mg_restrict_L" + std::to_string(l + 1), (Nl(l) + Nl(l + 1)) * tb(), [&] {
+        uf::k_restrict_lin<T><<<nb, uf::FT, 0, s>>>(lv[l], lv[l + 1], st);
+      });
+    }
   }
   // Up kernel of level l (the finest writes z and forms r.z).
   template <int SM>
   void rec_up(cudaStream_t s, int l, int mode, const uf::SmoothW<T>& om) {
     const std::string sl = std::to_string(l);
+    // linear transfers: the prolonged correction from level l + 1 (the tail
+    // forms that of the level above it)
+    if (lv[l].lin && l + 1 < P.tail_level) {
+      const unsigned nb = (unsigned)((Nl(l) + uf::FT - 1) / uf::FT);
+      L(s, "mg_prolong_L" + sl, (Nl(l) + Nl(l + 1)) * tb(), [&] {
+        uf::k_prolong_lin<T><<<nb, uf::FT, 0, s>>>(lv[l], lv[l + 1], st);
+      });
+    }
     int zc;
     const dim3 g = march_grid(l, &zc);
     if (l == 0)
@@ -690,7 +715,9 @@ class GridImpl final : public uf_grid {
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cudaLaunchKernelEx(&cfg, uf::k_mg_coarse<T, SM>, ca, tail, om, (const uf::SolveState*)st);
+        uf::TailArgs<T> ta = tail;
+        ta.rin = 1;   // the cluster's down legs leave the tail's right-hand side to the tail
+        cudaLaunchKernelEx(&cfg, uf::k_mg_coarse<T, SM>, ca, ta, om, (const uf::SolveState*)st);
       });
     } else {
       L(s, "mg_tail", (double)P.coarse_n * P.coarse_n * 8 + 2 * Nl(lt) * tb(),
@@ -1566,6 +1593,7 @@ class GridImpl final : public uf_grid {
     }
     V.tail_level = P.tail_level;
     V.tail = tail;
+    V.tail.rin = 1;   // batched launches form the tail's right-hand side in the tail
     V.tail_smem = P.tail_smem;
     int zc;
     const dim3 gc = chunk_grid(d.nx, d.ny, d.nz, &zc);
@@ -2271,6 +2299,7 @@ void uf_default_desc(uf_grid_desc* d) {
   d->precond = UF_PRECOND_MG; d->cg_tol = 0.0; d->cg_max_iter = 200;
   d->ai_omega = 1.65; d->mg_jacobi_omega = 6.0 / 7.0; d->mg_coarse_max = 512;
   d->mg_smoother = UF_SMOOTH_CHEBY;
+  d->mg_transfer = UF_TRANSFER_LINEAR;
   d->cg_stop_rule = UF_STOP_RESIDUAL;
 }
 

@@ -71,9 +71,21 @@ __device__ __forceinline__ T x_at(const Level<T>& L, int i, int j, int k) {
   return in_level(L, i, j, k) ? ldl(L.x + lidx(L, i, j, k)) : T(0);
 }
 
+template <typename T>
+__device__ __forceinline__ T coarse_resid(const Level<T>& L, int i, int j, int k) {
+  const T D = diag_xyz(L, i, j, k);
+  const T xv = ldl(L.x + lidx(L, i, j, k));
+  const T q = ldl(L.r + lidx(L, i, j, k)) * rdiag(D);
+  return resid(D, q, xv,
+               nb6(L.wx, x_at(L, i - 1, j, k), x_at(L, i + 1, j, k), L.wy, x_at(L, i, j - 1, k), x_at(L, i, j + 1, k),
+                   L.wz, x_at(L, i, j, k - 1), x_at(L, i, j, k + 1)));
+}
+
+// to_tail: C is the tail's first level, whose right-hand side the tail
+// forms itself from L's residual under linear transfers.
 template <typename T, int SM>
-__device__ __forceinline__ void coarse_down(const Level<T>& L, const Level<T>& C, const SmoothW<T>& W, int rank,
-                                            int nrank, cooperative_groups::cluster_group& cl) {
+__device__ __forceinline__ void coarse_down(const Level<T>& L, const Level<T>& C, const SmoothW<T>& W, bool to_tail,
+                                            int rank, int nrank, cooperative_groups::cluster_group& cl) {
   // pre-smoothing from zero (computeX of mg_down_body)
   cluster_cells(L.nx, L.ny, L.nz, rank, nrank, [&](int i, int j, int k) {
     const T qc = q_at(L, i, j, k);
@@ -82,6 +94,19 @@ __device__ __forceinline__ void coarse_down(const Level<T>& L, const Level<T>& C
     L.x[lidx(L, i, j, k)] = presmooth<SM>(qc, s, diag_xyz(L, i, j, k), W, ((i + j + k) & 1) == 0);
   });
   cl.sync();
+  if (L.lin) {   // residual into L.t, then the linear restriction (as k_restrict_lin)
+    cluster_cells(L.nx, L.ny, L.nz, rank, nrank,
+                  [&](int i, int j, int k) { L.t[lidx(L, i, j, k)] = coarse_resid(L, i, j, k); });
+    cl.sync();
+    if (!to_tail) {
+      cluster_cells(C.nx, C.ny, C.nz, rank, nrank, [&](int ci, int cj, int ck) {
+        C.r[lidx(C, ci, cj, ck)] =
+            restrict_lin(L, C, ci, cj, ck, [&](int i, int j, int k) { return ldl(L.t + lidx(L, i, j, k)); });
+      });
+      cl.sync();
+    }
+    return;
+  }
   // residual and summed restriction (children in the order of mg_down_body)
   const int fx = L.cx ? 2 : 1, fy = L.cy ? 2 : 1;
   cluster_cells(C.nx, C.ny, C.nz, rank, nrank, [&](int ci, int cj, int ck) {
@@ -91,16 +116,7 @@ __device__ __forceinline__ void coarse_down(const Level<T>& L, const Level<T>& C
       for (int dy = 0; dy < fy; ++dy)
         for (int dx = 0; dx < fx; ++dx) {
           const int i = ci * fx + dx, j = cj * fy + dy;
-          T res = 0;
-          if (in_level(L, i, j, k)) {
-            const T D = diag_xyz(L, i, j, k);
-            const T xv = ldl(L.x + lidx(L, i, j, k));
-            const T q = ldl(L.r + lidx(L, i, j, k)) * rdiag(D);
-            res = resid(D, q, xv,
-                        nb6(L.wx, x_at(L, i - 1, j, k), x_at(L, i + 1, j, k), L.wy, x_at(L, i, j - 1, k),
-                            x_at(L, i, j + 1, k), L.wz, x_at(L, i, j, k - 1), x_at(L, i, j, k + 1)));
-          }
-          sum += res;
+          sum += in_level(L, i, j, k) ? coarse_resid(L, i, j, k) : T(0);
         }
     }
     C.r[lidx(C, ci, cj, ck)] = sum;
@@ -114,6 +130,9 @@ __device__ __forceinline__ void coarse_up(const Level<T>& L, const Level<T>& C, 
   // t = x + P e, zero outside (commitT of mg_up_body)
   auto t_at = [&](int i, int j, int k) -> T {
     if (!in_level(L, i, j, k)) return T(0);
+    if (L.lin)
+      return ldl(L.x + lidx(L, i, j, k)) +
+             prolong_lin(L, C, i, j, k, [&](int a, int b, int c) { return ldl(C.t + lidx(C, a, b, c)); });
     const int pi = L.cx ? i >> 1 : i, pj = L.cy ? j >> 1 : j, pk = L.cz ? k >> 1 : k;
     return ldl(L.x + lidx(L, i, j, k)) + ldl(C.t + lidx(C, pi, pj, pk));
   };
@@ -144,7 +163,7 @@ __global__ void __launch_bounds__(CT) k_mg_coarse(const __grid_constant__ Coarse
   cg::cluster_group cl = cg::this_cluster();
   if (st->converged) return;   // set before this launch: the same in every CTA
   const int rank = (int)cl.block_rank(), nrank = (int)cl.num_blocks();
-  for (int m = A.cs; m < A.lt; ++m) coarse_down<T, SM>(A.lv[m], A.lv[m + 1], W, rank, nrank, cl);
+  for (int m = A.cs; m < A.lt; ++m) coarse_down<T, SM>(A.lv[m], A.lv[m + 1], W, m + 1 == A.lt, rank, nrank, cl);
   if (rank == 0) mg_tail_body<T, SM>(tail, W, st, vblock());
   cl.sync();
   for (int m = A.lt - 1; m >= A.cs; --m) coarse_up<T, SM>(A.lv[m], A.lv[m + 1], A.lu[m], W, rank, nrank, cl);

@@ -8,10 +8,14 @@
 //   (k_mg_down, k_mg_up and k_cg_dir_q march along z with rolling planes.)
 //   k_mg_down  : [finest level: CG update x += a d, r -= a q, ||r||^2]
 //                pre-smoothing from a zero guess, residual, summed
-//                restriction to the next level.            reads r (q, x, d)
-//   k_mg_up    : coarse-grid correction (piecewise-constant prolongation) and
-//                the post-smoothing passes; on the finest level also r.z and
-//                the CG beta.                              reads x_pre, e, r
+//                restriction to the next level (under linear transfers: the
+//                residual, stored for k_restrict_lin).     reads r (q, x, d)
+//   k_mg_up    : coarse-grid correction (piecewise-constant prolongation, or
+//                the correction k_prolong_lin prolonged linearly) and the
+//                post-smoothing passes; on the finest level also r.z and the
+//                CG beta.                                  reads x_pre, e, r
+//   k_restrict_lin, k_prolong_lin : the linear transfers between levels
+//                below the finest, one pass each.
 //   k_mg_tail  : one block runs the whole V-cycle below a level that fits in
 //                shared memory; coarsest level by its dense FP64 inverse.
 //   k_cg_dir_q : d = z + beta d_old and q = A d, plus d.q and alpha.
@@ -158,6 +162,98 @@ __device__ __forceinline__ T nb6(T wx, T a1, T a2, T wy, T b1, T b2, T wz, T c1,
 template <typename T>
 __device__ __forceinline__ T resid(T D, T q, T x, T nbsum) {
   return fma_rn(D, add_rn(q, -x), nbsum);
+}
+
+// Cell-centred linear transfers between a level (n_f cells along an axis)
+// and the next coarser one (n_c = ceil(n_f / 2)).  Prolongation along a
+// halved axis: fine cell i takes 3/4 of its parent p = i/2 and 1/4 of the
+// parent's neighbour on its own side (p - 1 for even i, p + 1 for odd i);
+// beyond the level that neighbour is a ghost, the parent mirrored (dp/dn =
+// 0: weight 3/4 + 1/4 on p) or negated on an outlet side (p = 0 on the
+// face: 3/4 - 1/4).  An axis that is not halved maps cell to cell.  The
+// restriction is the transpose: coarse cell p gathers its children 2p and
+// 2p + 1 (3/4, or the ghost-folded weight at the level's ends) and the
+// outer neighbours 2p - 1 and 2p + 2 (1/4).
+// Each transfer value is one FMA chain over the slots inside the level, z
+// outermost, then y, then x (slot s is cell base + s), with explicit
+// rounding; every weight and every product of three is exact in binary.  So
+// a value is the same bit for bit wherever it is formed (the pass kernels,
+// the tail, the cluster V-cycle).
+struct Taps {
+  int base;    // cell index of slot 0
+  int valid;   // bit s: slot s takes part
+  float w[4];
+};
+// Prolongation taps of fine cell i along an axis (slots p - 1, p, p + 1).
+__device__ __forceinline__ Taps taps_p(int i, int halved, int nc, bool out_lo, bool out_hi) {
+  Taps t;
+  t.w[0] = t.w[2] = t.w[3] = 0.25f;
+  if (!halved) {
+    t.base = i - 1; t.valid = 2; t.w[1] = 1.0f;
+    return t;
+  }
+  const int p = i >> 1;
+  t.base = p - 1;
+  if (i & 1) {   // neighbour p + 1
+    const bool in = p + 1 < nc;
+    t.valid = in ? 6 : 2;
+    t.w[1] = in ? 0.75f : (out_hi ? 0.5f : 1.0f);
+  } else {       // neighbour p - 1
+    const bool in = p >= 1;
+    t.valid = in ? 3 : 2;
+    t.w[1] = in ? 0.75f : (out_lo ? 0.5f : 1.0f);
+  }
+  return t;
+}
+// Restriction taps of coarse cell p along an axis of nf fine cells (slots
+// 2p - 1, 2p, 2p + 1, 2p + 2).
+__device__ __forceinline__ Taps taps_r(int p, int halved, int nf, int nc, bool out_lo, bool out_hi) {
+  Taps t;
+  t.w[0] = t.w[3] = 0.25f;
+  if (!halved) {
+    t.base = p - 1; t.valid = 2; t.w[1] = 1.0f; t.w[2] = 0.0f;
+    return t;
+  }
+  t.base = 2 * p - 1;
+  t.valid = (p >= 1 ? 1 : 0) | 2 | (2 * p + 1 < nf ? 4 : 0) | (2 * p + 2 < nf ? 8 : 0);
+  t.w[1] = p == 0 ? (out_lo ? 0.5f : 1.0f) : 0.75f;
+  t.w[2] = p == nc - 1 ? (out_hi ? 0.5f : 1.0f) : 0.75f;
+  return t;
+}
+// (loops unrolled over the four slots and predicated, so the taps stay in
+// registers)
+template <typename T, typename Get>
+__device__ __forceinline__ T tap_sum(const Taps& tx, const Taps& ty, const Taps& tz, Get get) {
+  T acc = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    if (!((tz.valid >> c) & 1)) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      if (!((ty.valid >> b) & 1)) continue;
+      const T wzy = (T)tz.w[c] * (T)ty.w[b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        if (!((tx.valid >> a) & 1)) continue;
+        acc = fma_rn(wzy * (T)tx.w[a], get(tx.base + a, ty.base + b, tz.base + c), acc);
+      }
+    }
+  }
+  return acc;
+}
+// (P e)(i, j, k) on fine level F from the coarse values get(ci, cj, ck) of C.
+template <typename T, typename Get>
+__device__ __forceinline__ T prolong_lin(const Level<T>& F, const Level<T>& C, int i, int j, int k, Get get) {
+  const int m = F.out_mask;
+  return tap_sum<T>(taps_p(i, F.cx, C.nx, m & 1, m & 2), taps_p(j, F.cy, C.ny, m & 4, m & 8),
+                    taps_p(k, F.cz, C.nz, m & 16, m & 32), get);
+}
+// (R r)(ci, cj, ck) on coarse level C from the fine values get(i, j, k) of F.
+template <typename T, typename Get>
+__device__ __forceinline__ T restrict_lin(const Level<T>& F, const Level<T>& C, int ci, int cj, int ck, Get get) {
+  const int m = F.out_mask;
+  return tap_sum<T>(taps_r(ci, F.cx, F.nx, C.nx, m & 1, m & 2), taps_r(cj, F.cy, F.ny, C.ny, m & 4, m & 8),
+                    taps_r(ck, F.cz, F.nz, C.nz, m & 16, m & 32), get);
 }
 
 // Pre-smoothing from zero with q = r/D staged: weighted Jacobi x2 = pa q_c +
@@ -339,19 +435,23 @@ __device__ __forceinline__ void mg_down_body(const Level<T>& F, const Level<T>& 
       }
     }
     (void)opar;
-    sR[k & 1][tid] = res;
-    if (!F.cz || (k & 1)) {
-      __syncthreads();
-      const int kc = F.cz ? (k >> 1) : k;
-      for (int e = tid; e < cnx * cny; e += FT) {
-        const int cxl = e % cnx, cyl = e / cnx;
-        const int ci = i0 / fx + cxl, cj = j0 / fy + cyl;
-        if (!in_level(C, ci, cj, kc)) continue;
-        T sum = 0;
-        for (int dz = F.cz ? 1 : 0; dz >= 0; --dz)
-          for (int dy = 0; dy < fy; ++dy)
-            for (int dx = 0; dx < fx; ++dx) sum += sR[(k - dz) & 1][(cxl * fx + dx) + TX * (cyl * fy + dy)];
-        C.r[lidx(C, ci, cj, kc)] = sum;
+    if (!CG && F.lin) {   // linear transfers: the restriction runs as its own pass over the stored residual
+      if (own) F.t[oc] = res;
+    } else {
+      sR[k & 1][tid] = res;
+      if (!F.cz || (k & 1)) {
+        __syncthreads();
+        const int kc = F.cz ? (k >> 1) : k;
+        for (int e = tid; e < cnx * cny; e += FT) {
+          const int cxl = e % cnx, cyl = e / cnx;
+          const int ci = i0 / fx + cxl, cj = j0 / fy + cyl;
+          if (!in_level(C, ci, cj, kc)) continue;
+          T sum = 0;
+          for (int dz = F.cz ? 1 : 0; dz >= 0; --dz)
+            for (int dy = 0; dy < fy; ++dy)
+              for (int dx = 0; dx < fx; ++dx) sum += sR[(k - dz) & 1][(cxl * fx + dx) + TX * (cyl * fy + dy)];
+          C.r[lidx(C, ci, cj, kc)] = sum;
+        }
       }
     }
     const int xs_t = xs_m;
@@ -397,6 +497,65 @@ __global__ void __launch_bounds__(FT) k_mg_down(Level<T> F, Level<T> C, SmoothW<
   mg_down_body<T, SM, CG>(F, C, W, zc, x, d0, d1, q, partials, st, cond, use_cond, nullptr, vblock());
 }
 
+
+// ------------------------------------------------------- restriction -----
+// Linear transfers (F.lin): the down kernel of F stores its residual in F.t;
+// before the down kernel of the next level C, C.r = R F.t, and before the
+// up kernel of F, F.e = P C.t (the up kernel reads it as it would read the
+// parent's value).  One thread per cell of the level written (k_restrict_lin,
+// k_prolong_lin), or, in a batch, per column of a march tile of level C.
+template <typename T>
+__device__ __forceinline__ void restrict_lin_at(const Level<T>& F, const Level<T>& C, int ci, int cj, int ck) {
+  C.r[lidx(C, ci, cj, ck)] = restrict_lin(F, C, ci, cj, ck, [&](int i, int j, int k) { return F.t[lidx(F, i, j, k)]; });
+}
+template <typename T>
+__device__ __forceinline__ void prolong_lin_at(const Level<T>& F, const Level<T>& C, int i, int j, int k) {
+  F.e[lidx(F, i, j, k)] = prolong_lin(F, C, i, j, k, [&](int a, int b, int c) { return C.t[lidx(C, a, b, c)]; });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FT) k_restrict_lin(Level<T> F, Level<T> C, const SolveState* st) {
+  if (st->converged) return;
+  const long long e = (long long)blockIdx.x * FT + threadIdx.x;
+  if (e >= (long long)C.nx * C.ny * C.nz) return;
+  const int ci = (int)(e % C.nx), cj = (int)((e / C.nx) % C.ny), ck = (int)(e / ((long long)C.nx * C.ny));
+  restrict_lin_at(F, C, ci, cj, ck);
+}
+template <typename T>
+__global__ void __launch_bounds__(FT) k_prolong_lin(Level<T> F, Level<T> C, const SolveState* st) {
+  if (st->converged) return;
+  const long long e = (long long)blockIdx.x * FT + threadIdx.x;
+  if (e >= (long long)F.nx * F.ny * F.nz) return;
+  const int i = (int)(e % F.nx), j = (int)((e / F.nx) % F.ny), k = (int)(e / ((long long)F.nx * F.ny));
+  prolong_lin_at(F, C, i, j, k);
+}
+
+// The same over a march tile of level C (batched launches).
+template <typename T>
+__device__ __forceinline__ void restrict_lin_body(const Level<T>& F, const Level<T>& C, int zc, const SolveState* st,
+                                                  const VBlock& vb) {
+  if (st->converged) return;
+  const int ci = vb.x * TX + (threadIdx.x & (TX - 1)), cj = vb.y * TY + threadIdx.x / TX;
+  const int k0 = vb.z * zc, kend = min(C.nz, k0 + zc);
+  if (ci >= C.nx || cj >= C.ny) return;
+  for (int ck = k0; ck < kend; ++ck) restrict_lin_at(F, C, ci, cj, ck);
+}
+template <typename T>
+__device__ __forceinline__ void prolong_lin_body(const Level<T>& F, const Level<T>& C, int zc, const SolveState* st,
+                                                 const VBlock& vb) {
+  if (st->converged) return;
+  const int ci = vb.x * TX + (threadIdx.x & (TX - 1)), cj = vb.y * TY + threadIdx.x / TX;
+  const int k0 = vb.z * zc, kend = min(C.nz, k0 + zc);
+  if (ci >= C.nx || cj >= C.ny) return;
+  const int fx = F.cx ? 2 : 1, fy = F.cy ? 2 : 1, fz = F.cz ? 2 : 1;
+  for (int ck = k0; ck < kend; ++ck)
+    for (int dz = 0; dz < fz; ++dz)
+      for (int dy = 0; dy < fy; ++dy)
+        for (int dx = 0; dx < fx; ++dx) {
+          const int i = ci * fx + dx, j = cj * fy + dy, k = ck * fz + dz;
+          if (in_level(F, i, j, k)) prolong_lin_at(F, C, i, j, k);
+        }
+}
 
 // -------------------------------------------------------------- up -------
 // Same z-march: t = x_pre + e(parent) on tile + halo 2 (ring of 4), first
@@ -449,7 +608,8 @@ __device__ __forceinline__ void mg_up_body(const Level<T>& F, const Level<T>& C,
       pe[h] = 0;
       if (kin && pt[h].ok) {
         px[h] = F.x[(size_t)k * PS + pt[h].off];
-        pe[h] = C.t[(size_t)pk * PSC + poff[h]];
+        // (linear transfers: the prolonged correction, formed before this kernel)
+        pe[h] = F.lin ? F.e[(size_t)k * PS + pt[h].off] : C.t[(size_t)pk * PSC + poff[h]];
       }
     }
   };
@@ -582,6 +742,8 @@ struct TailArgs {
   int cr_off;            // byte offset of the compact FP64 right-hand side of the coarsest solve
   const double* ainv;
   int n_coarse;
+  int rin;   // linear transfers above the tail: 1 = form the first level's right-hand side from the
+             // residual of the level above here, 0 = it is in lv[lt].r already
 };
 
 template <typename T, int SM>
@@ -610,9 +772,17 @@ __device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, const SmoothW
     int X, P, NB;
     geom(A.lt, X, P, NB);
     T* r = S + A.off[A.lt];
-    tail_cells(L.nx, L.ny, L.nz, [&](int i, int j, int k) {
-      r[(i + 1) + X * (j + 1) + P * (k + 1)] = L.r[lidx(L, i, j, k)];
-    });
+    if (A.rin && A.lt > 0 && A.lv[A.lt - 1].lin) {   // the linear restriction of the level above's residual
+      const Level<T>& Fa = A.lv[A.lt - 1];
+      tail_cells(L.nx, L.ny, L.nz, [&](int i, int j, int k) {
+        r[(i + 1) + X * (j + 1) + P * (k + 1)] =
+            restrict_lin(Fa, L, i, j, k, [&](int a, int b, int c) { return Fa.t[lidx(Fa, a, b, c)]; });
+      });
+    } else {
+      tail_cells(L.nx, L.ny, L.nz, [&](int i, int j, int k) {
+        r[(i + 1) + X * (j + 1) + P * (k + 1)] = L.r[lidx(L, i, j, k)];
+      });
+    }
   }
   __syncthreads();
   for (int m = A.lt; m < A.nl - 1; ++m) {
@@ -636,6 +806,21 @@ __device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, const SmoothW
     });
     __syncthreads();
     T* rc = S + A.off[m + 1];
+    if (L.lin) {
+      // residual of every cell into u (no longer needed), then the linear restriction
+      tail_cells(L.nx, L.ny, L.nz, [&](int i, int j, int k) {
+        const int b = (i + 1) + X * (j + 1) + P * (k + 1);
+        const T nb = nb6(L.wx, a[b - 1], a[b + 1], L.wy, a[b - X], a[b + X], L.wz, a[b - P], a[b + P]);
+        u[b] = add_rn(fma_rn(-diag_of(L, i, j, k), a[b], r[b]), nb);
+      });
+      __syncthreads();
+      tail_cells(Cc.nx, Cc.ny, Cc.nz, [&](int ci, int cj, int ck) {
+        rc[(ci + 1) + CX * (cj + 1) + CP * (ck + 1)] =
+            restrict_lin(L, Cc, ci, cj, ck, [&](int i, int j, int k) { return u[(i + 1) + X * (j + 1) + P * (k + 1)]; });
+      });
+      __syncthreads();
+      continue;
+    }
     tail_cells(Cc.nx, Cc.ny, Cc.nz, [&](int ci, int cj, int ck) {
       const int i0 = L.cx ? 2 * ci : ci, i1 = L.cx ? min(2 * ci + 1, L.nx - 1) : ci;
       const int j0 = L.cy ? 2 * cj : cj, j1 = L.cy ? min(2 * cj + 1, L.ny - 1) : cj;
@@ -695,9 +880,16 @@ __device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, const SmoothW
     T* a = r + NB;
     T* u = a + NB;
     const T* ec = S + A.off[m + 1] + CNB;
+    const Level<T>& Cc = A.lv[m + 1];
     tail_cells(L.nx, L.ny, L.nz, [&](int i, int j, int k) {   // t = x + P e (in place)
-      const int pi = L.cx ? i >> 1 : i, pj = L.cy ? j >> 1 : j, pk = L.cz ? k >> 1 : k;
-      a[(i + 1) + X * (j + 1) + P * (k + 1)] += ec[(pi + 1) + CX * (pj + 1) + CP * (pk + 1)];
+      T e;
+      if (L.lin) {
+        e = prolong_lin(L, Cc, i, j, k, [&](int a2, int b2, int c2) { return ec[(a2 + 1) + CX * (b2 + 1) + CP * (c2 + 1)]; });
+      } else {
+        const int pi = L.cx ? i >> 1 : i, pj = L.cy ? j >> 1 : j, pk = L.cz ? k >> 1 : k;
+        e = ec[(pi + 1) + CX * (pj + 1) + CP * (pk + 1)];
+      }
+      a[(i + 1) + X * (j + 1) + P * (k + 1)] += e;
     });
     __syncthreads();
     tail_cells(L.nx, L.ny, L.nz, [&](int i, int j, int k) {
@@ -721,6 +913,13 @@ __device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, const SmoothW
     tail_cells(L.nx, L.ny, L.nz, [&](int i, int j, int k) {
       L.t[lidx(L, i, j, k)] = a[(i + 1) + X * (j + 1) + P * (k + 1)];
     });
+    if (A.lt > 0 && A.lv[A.lt - 1].lin) {   // the level above's prolonged correction
+      const Level<T>& Fa = A.lv[A.lt - 1];
+      tail_cells(Fa.nx, Fa.ny, Fa.nz, [&](int i, int j, int k) {
+        Fa.e[lidx(Fa, i, j, k)] =
+            prolong_lin(Fa, L, i, j, k, [&](int a2, int b2, int c2) { return a[(a2 + 1) + X * (b2 + 1) + P * (c2 + 1)]; });
+      });
+    }
   }
 }
 

@@ -39,6 +39,9 @@ struct Level {
   T* x;
   T* t;
   T* r_alt;            // finest level of the fused V-cycle: r ping-pongs with the CG iteration parity
+  int lin;             // multigrid: 1 if the transfers to the next coarser level are cell-centred
+                       // linear (restriction = transpose of the prolongation), 0 piecewise constant
+  T* e;                // lin: the prolonged coarse correction P t_{l+1} on this level
 };
 
 // Residual buffer holding the current r after `iter` CG iterations.

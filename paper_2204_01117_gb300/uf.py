@@ -31,6 +31,7 @@ F32, F64 = 0, 1
 PRECOND = {"mg": 0, "ai1": 1, "jacobi": 2, "none": 3, "ai2": 4}
 STOP_RULE = {"residual": 0, "paper": 1}
 SMOOTHER = {"jacobi": 0, "rbgs": 1, "cheby": 2}
+TRANSFER = {"constant": 0, "linear": 1}
 FIELDS = {"u": 0, "v": 1, "w": 2, "p": 3, "k": 4, "omega": 5, "phi": 6, "nut": 7}
 
 
@@ -51,7 +52,7 @@ class GridDesc(ctypes.Structure):
         ("precond", ctypes.c_int), ("cg_tol", ctypes.c_double), ("cg_max_iter", ctypes.c_int),
         ("ai_omega", ctypes.c_double), ("mg_jacobi_omega", ctypes.c_double),
         ("mg_coarse_max", ctypes.c_int), ("mg_smoother", ctypes.c_int),
-        ("cg_stop_rule", ctypes.c_int),
+        ("cg_stop_rule", ctypes.c_int), ("mg_transfer", ctypes.c_int),
     ]
 
 
@@ -276,6 +277,8 @@ def default_desc(**overrides) -> GridDesc:
             v = SMOOTHER[v]
         if k == "cg_stop_rule" and isinstance(v, str):
             v = STOP_RULE[v]
+        if k == "mg_transfer" and isinstance(v, str):
+            v = TRANSFER[v]
         if not hasattr(d, k):
             raise TypeError(f"unknown grid parameter {k!r}")
         setattr(d, k, v)

@@ -74,6 +74,8 @@ def test_enums_match_the_header():
     assert v["UF_STOP_RESIDUAL"] == uf.STOP_RULE["residual"] and v["UF_STOP_PAPER"] == uf.STOP_RULE["paper"]
     for name, val in uf.SMOOTHER.items():
         assert v["UF_SMOOTH_" + name.upper()] == val, name
+    for name, val in uf.TRANSFER.items():
+        assert v["UF_TRANSFER_" + name.upper()] == val, name
     for name, val in uf.FIELDS.items():
         assert v["UF_FIELD_" + name.upper()] == val, name
     for i, name in enumerate(uf.STATUS_NAMES):

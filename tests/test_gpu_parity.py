@@ -71,13 +71,16 @@ def test_poisson_operator(precision, dims, deg):
     assert rel(y, ref) <= tol
 
 
-@pytest.mark.parametrize("precond", ["mg", "mg-rbgs", "mg-cheby", "ai1", "jacobi", "none"])
+@pytest.mark.parametrize("precond", ["mg", "mg-rbgs", "mg-cheby", "mg-constant", "ai1", "jacobi", "none"])
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_poisson_solve(precond, precision):
     nx, ny, nz = 45, 37, 11
     tol = 1e-12 if precision == "f64" else 1e-7
     o = oracle.Oracle(nx, ny, nz, wind_dir_deg=30.0)
-    extra = {"mg_smoother": precond.split("-")[1]} if precond.startswith("mg-") else {}
+    extra = {}
+    if precond.startswith("mg-"):
+        v = precond.split("-")[1]
+        extra = {"mg_transfer": v} if v in uf.TRANSFER else {"mg_smoother": v}
     g = uf.Grid(nx, ny, nz, precision=precision, wind_dir_deg=30.0, precond=precond.split("-")[0], cg_tol=tol,
                 cg_max_iter=5000, **extra)
     b = np.random.default_rng(1).standard_normal((nz, ny, nx))
@@ -87,6 +90,37 @@ def test_poisson_solve(precond, precision):
     assert r <= tol
     x = g.get_state("p")
     assert rel(x, ref) <= (1e-9 if precision == "f64" else 5e-5), (precond, it)
+
+
+@pytest.mark.parametrize("dims, deg", [((96, 80, 32), 0.0), ((96, 80, 32), 200.0), ((96, 80, 32), 290.0),
+                                       ((90, 78, 24), 30.0)])
+def test_linear_transfers_reach_the_solution(dims, deg):
+    """Multigrid with cell-centred linear transfers below level 1 (the
+    default) against piecewise-constant transfers on every level: both
+    reach the oracle's CG solution.  Where every level below the finest
+    halves evenly (96 x 80 x 32) the linear ones take fewer CG iterations
+    (the numpy model of this V-cycle: 9 against 11 on random right-hand
+    sides at 128 x 128 x 32); wind directions with outlets on the high and
+    on the low sides exercise the negated ghosts.  On levels of odd size
+    (90 x 78 x 24: 45 x 39 x 12, 23 x 20 x 6) the coarse cell at the odd
+    end has one child, the interpolation is less accurate there, and the
+    count may be one higher."""
+    nx, ny, nz = dims
+    o = oracle.Oracle(nx, ny, nz, wind_dir_deg=deg)
+    b = np.random.default_rng(7).standard_normal((nz, ny, nx))
+    ref, _, _ = o.cg(b, tol=1e-13)
+    its = {}
+    for tr in ("constant", "linear"):
+        g = uf.Grid(nx, ny, nz, precision="f64", wind_dir_deg=deg, cg_tol=1e-10, cg_max_iter=500, mg_transfer=tr)
+        g.set_state("p", 0.0)
+        its[tr], r = g.poisson_solve(b)
+        assert r <= 1e-10
+        assert rel(g.get_state("p"), ref) <= 1e-8, (tr, its)
+        g.close()
+    if nx % 8 == 0 and ny % 8 == 0 and nz % 8 == 0:
+        assert its["linear"] < its["constant"], its
+    else:
+        assert its["linear"] <= its["constant"] + 1, its
 
 
 def test_preconditioner_iteration_ordering():
