@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace uf {
 
 enum SideType { INFLOW = 0, OUTFLOW = 1, SLIP = 2, NOSLIP = 3 };
