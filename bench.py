@@ -190,6 +190,25 @@ def ncu_traffic(kernel_label: str):
     return None
 
 
+def dominant_kernel(kernels: dict, prof_iters: int, mean_iters: float):
+    """The kernel with the most time in an average timed step, and its share.
+
+    The eagerly profiled step ran prof_iters CG iterations, the timed steps
+    mean_iters on average; as in step_traffic, a kernel that launched at
+    least prof_iters times runs once per iteration plus its fixed launches,
+    so its time per step is its mean launch time x (fixed launches +
+    mean_iters).  (Ranking by the profiled step alone would depend on that
+    one step's iteration count.)  Returns (label, entry, ms per step, share)."""
+    per_step = {}
+    for name, k in kernels.items():
+        n = int(k["launches"])
+        avg = float(k["total_ms"]) / max(n, 1)
+        runs = (n - prof_iters + mean_iters) if (prof_iters > 0 and n >= prof_iters) else n
+        per_step[name] = avg * runs
+    name = max(per_step, key=per_step.get)
+    return name, kernels[name], per_step[name], per_step[name] / sum(per_step.values())
+
+
 def step_traffic(kernels: dict, prof_iters: int, mean_iters: float, ms_per_step: float, peak: float,
                  cells: int) -> dict:
     """Algorithmic bytes of one whole step and their rate over the
@@ -396,10 +415,9 @@ def batched_leg(steps: int = 10, peak: float = 6790.0, peak_kind: str = "measure
     prof_iters = int(prof.get("b_cg_dir_q", {}).get("launches", 0))
     mean_iters = sum(c * x.cg_iters for c, x in zip(inst_cells, st)) / float(sum(inst_cells))
     step_bytes = step_traffic(prof, prof_iters, mean_iters, ms_b / steps, peak, cells)
-    dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
+    dom_name, dom, _, dom_share = dominant_kernel(prof, prof_iters, mean_iters)
     avg_ms = dom["total_ms"] / dom["launches"]
     achieved = dom["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
-    total_prof = sum(k["total_ms"] for k in prof.values())
     b.close()
     del b
     torch.cuda.empty_cache()
@@ -437,7 +455,7 @@ def batched_leg(steps: int = 10, peak: float = 6790.0, peak_kind: str = "measure
         "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
                      "step": step_bytes,
-                     "kernel_share_of_step": dom["total_ms"] / total_prof,
+                     "kernel_share_of_step": dom_share,
                      "bytes_per_launch": dom["bytes_per_launch"], "avg_launch_us": avg_ms * 1e3},
     }
 
@@ -933,13 +951,12 @@ def run_ours(args):
 
     # -- per-kernel CUDA-event timing of one eagerly launched step ----------
     pst, kernels = g.profile_step()
-    dom_name, dom = max(kernels.items(), key=lambda kv: kv[1]["total_ms"])
+    dom_name, dom, _, dom_share = dominant_kernel(kernels, pst.cg_iters, iters_timed / args.steps)
     avg_ms = dom["total_ms"] / dom["launches"]
     achieved = dom["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
     peaks, peak_kind = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
     traffic = ncu_traffic(dom_name)
-    total_prof = sum(k["total_ms"] for k in kernels.values())
 
     if rank != 0:
         if pg:
@@ -955,7 +972,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"hbm_gbs of {peak_kind}",
-                     "kernel_share_of_step": dom["total_ms"] / total_prof,
+                     "kernel_share_of_step": dom_share,
                      "bytes_per_launch": dom["bytes_per_launch"], "avg_launch_us": avg_ms * 1e3,
                      "step": step_traffic(kernels, pst.cg_iters, iters_timed / args.steps, ms / args.steps, peak,
                                           sc.cells)},

@@ -655,7 +655,7 @@ class GridImpl final : public uf_grid {
     // linear transfers: the right-hand side of level l + 1 from the stored
     // residual (here also that of the tail's first level: tail.rin = 0)
     if (lv[l].lin && l + 1 <= P.tail_level) {
-      const unsigned nb = (unsigned)((Nl(l + 1) + uf::FT - 1) / uf::FT);
+      const unsigned nb = (unsigned)((4 * Nl(l + 1) + uf::FT - 1) / uf::FT);   // four threads per cell
       L(s, "mg_restrict_L" + std::to_string(l + 1), (Nl(l) + Nl(l + 1)) * tb(), [&] {
         uf::k_restrict_lin<T><<<nb, uf::FT, 0, s>>>(lv[l], lv[l + 1], st);
       });

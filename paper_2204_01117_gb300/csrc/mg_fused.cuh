@@ -248,12 +248,49 @@ __device__ __forceinline__ T prolong_lin(const Level<T>& F, const Level<T>& C, i
   return tap_sum<T>(taps_p(i, F.cx, C.nx, m & 1, m & 2), taps_p(j, F.cy, C.ny, m & 4, m & 8),
                     taps_p(k, F.cz, C.nz, m & 16, m & 32), get);
 }
-// (R r)(ci, cj, ck) on coarse level C from the fine values get(i, j, k) of F.
+// (R r)(ci, cj, ck) on coarse level C from the fine values get(i, j, k) of F,
+// as four partial sums, one per z slot (each an FMA chain over y, then x),
+// added in slot order: ((P0 + P1) + P2) + P3 (an absent slot is 0).  The
+// partials can be formed by four threads (k_restrict_lin, the tail) or one
+// after another (restrict_lin), with the same result.
+template <typename T, typename Get>
+__device__ __forceinline__ T restrict_partial(const Level<T>& F, const Level<T>& C, int ci, int cj, int ck, int c,
+                                              Get get) {
+  const int m = F.out_mask;
+  const Taps tz = taps_r(ck, F.cz, F.nz, C.nz, m & 16, m & 32);
+  if (!((tz.valid >> c) & 1)) return T(0);
+  const Taps tx = taps_r(ci, F.cx, F.nx, C.nx, m & 1, m & 2), ty = taps_r(cj, F.cy, F.ny, C.ny, m & 4, m & 8);
+  const T wz = (T)(c == 0 ? tz.w[0] : c == 1 ? tz.w[1] : c == 2 ? tz.w[2] : tz.w[3]);   // (no indexed array)
+  T acc = 0;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    if (!((ty.valid >> b) & 1)) continue;
+    const T wzy = wz * (T)ty.w[b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (!((tx.valid >> a) & 1)) continue;
+      acc = fma_rn(wzy * (T)tx.w[a], get(tx.base + a, ty.base + b, tz.base + c), acc);
+    }
+  }
+  return acc;
+}
+template <typename T>
+__device__ __forceinline__ T combine_partials(T p0, T p1, T p2, T p3) {
+  return add_rn(add_rn(add_rn(p0, p1), p2), p3);
+}
 template <typename T, typename Get>
 __device__ __forceinline__ T restrict_lin(const Level<T>& F, const Level<T>& C, int ci, int cj, int ck, Get get) {
-  const int m = F.out_mask;
-  return tap_sum<T>(taps_r(ci, F.cx, F.nx, C.nx, m & 1, m & 2), taps_r(cj, F.cy, F.ny, C.ny, m & 4, m & 8),
-                    taps_r(ck, F.cz, F.nz, C.nz, m & 16, m & 32), get);
+  return combine_partials(restrict_partial(F, C, ci, cj, ck, 0, get), restrict_partial(F, C, ci, cj, ck, 1, get),
+                          restrict_partial(F, C, ci, cj, ck, 2, get), restrict_partial(F, C, ci, cj, ck, 3, get));
+}
+// The same with the four partials on four adjacent lanes (lane & 3 = slot;
+// every lane of the warp calls this): returns the sum on every lane.
+template <typename T>
+__device__ __forceinline__ T quad_combine(T part) {
+  const int qb = (threadIdx.x & 31) & ~3;
+  const T p0 = __shfl_sync(0xffffffffu, part, qb), p1 = __shfl_sync(0xffffffffu, part, qb + 1);
+  const T p2 = __shfl_sync(0xffffffffu, part, qb + 2), p3 = __shfl_sync(0xffffffffu, part, qb + 3);
+  return combine_partials(p0, p1, p2, p3);
 }
 
 // Pre-smoothing from zero with q = r/D staged: weighted Jacobi x2 = pa q_c +
@@ -513,13 +550,19 @@ __device__ __forceinline__ void prolong_lin_at(const Level<T>& F, const Level<T>
   F.e[lidx(F, i, j, k)] = prolong_lin(F, C, i, j, k, [&](int a, int b, int c) { return C.t[lidx(C, a, b, c)]; });
 }
 
+// Four threads per coarse cell (one per z slot of the restriction).
 template <typename T>
 __global__ void __launch_bounds__(FT) k_restrict_lin(Level<T> F, Level<T> C, const SolveState* st) {
   if (st->converged) return;
-  const long long e = (long long)blockIdx.x * FT + threadIdx.x;
-  if (e >= (long long)C.nx * C.ny * C.nz) return;
-  const int ci = (int)(e % C.nx), cj = (int)((e / C.nx) % C.ny), ck = (int)(e / ((long long)C.nx * C.ny));
-  restrict_lin_at(F, C, ci, cj, ck);
+  const long long e = ((long long)blockIdx.x * FT + threadIdx.x) >> 2;
+  const int slot = threadIdx.x & 3;
+  const bool in = e < (long long)C.nx * C.ny * C.nz;
+  const int ci = in ? (int)(e % C.nx) : 0, cj = in ? (int)((e / C.nx) % C.ny) : 0;
+  const int ck = in ? (int)(e / ((long long)C.nx * C.ny)) : 0;
+  const T part = in ? restrict_partial(F, C, ci, cj, ck, slot, [&](int i, int j, int k) { return F.t[lidx(F, i, j, k)]; })
+                    : T(0);
+  const T sum = quad_combine(part);   // (every lane of the warp takes part)
+  if (in && slot == 0) C.r[lidx(C, ci, cj, ck)] = sum;
 }
 template <typename T>
 __global__ void __launch_bounds__(FT) k_prolong_lin(Level<T> F, Level<T> C, const SolveState* st) {
@@ -734,6 +777,22 @@ __device__ __forceinline__ void tail_cells(int nx, int ny, int nz, F f) {
       for (int i = tx; i < nx; i += 16) f(i, j, k);
 }
 
+// The cells of level C, four threads per cell (slot = lane & 3): part(i, j,
+// k, slot) forms a partial on each, and put(i, j, k, sum) stores their sum
+// (quad_combine; the loop runs over whole warps so that every lane takes
+// part in the shuffles).
+template <typename T, typename Part, typename Put>
+__device__ __forceinline__ void tail_quads(const Level<T>& C, Part part, Put put) {
+  const int nc = C.nx * C.ny * C.nz, n4 = ((4 * nc + 31) / 32) * 32;
+  for (int e = threadIdx.x; e < n4; e += TAIL_T) {
+    const int cell = e >> 2;
+    const bool in = cell < nc;
+    const int i = in ? cell % C.nx : 0, j = in ? (cell / C.nx) % C.ny : 0, k = in ? cell / (C.nx * C.ny) : 0;
+    const T sum = quad_combine(in ? part(i, j, k, e & 3) : T(0));
+    if (in && (e & 3) == 0) put(i, j, k, sum);
+  }
+}
+
 template <typename T>
 struct TailArgs {
   Level<T> lv[MAX_LEVELS];
@@ -774,10 +833,9 @@ __device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, const SmoothW
     T* r = S + A.off[A.lt];
     if (A.rin && A.lt > 0 && A.lv[A.lt - 1].lin) {   // the linear restriction of the level above's residual
       const Level<T>& Fa = A.lv[A.lt - 1];
-      tail_cells(L.nx, L.ny, L.nz, [&](int i, int j, int k) {
-        r[(i + 1) + X * (j + 1) + P * (k + 1)] =
-            restrict_lin(Fa, L, i, j, k, [&](int a, int b, int c) { return Fa.t[lidx(Fa, a, b, c)]; });
-      });
+      tail_quads(L, [&](int i, int j, int k, int slot) {
+        return restrict_partial(Fa, L, i, j, k, slot, [&](int a, int b, int c) { return Fa.t[lidx(Fa, a, b, c)]; });
+      }, [&](int i, int j, int k, T sum) { r[(i + 1) + X * (j + 1) + P * (k + 1)] = sum; });
     } else {
       tail_cells(L.nx, L.ny, L.nz, [&](int i, int j, int k) {
         r[(i + 1) + X * (j + 1) + P * (k + 1)] = L.r[lidx(L, i, j, k)];
@@ -814,10 +872,10 @@ __device__ __forceinline__ void mg_tail_body(const TailArgs<T>& A, const SmoothW
         u[b] = add_rn(fma_rn(-diag_of(L, i, j, k), a[b], r[b]), nb);
       });
       __syncthreads();
-      tail_cells(Cc.nx, Cc.ny, Cc.nz, [&](int ci, int cj, int ck) {
-        rc[(ci + 1) + CX * (cj + 1) + CP * (ck + 1)] =
-            restrict_lin(L, Cc, ci, cj, ck, [&](int i, int j, int k) { return u[(i + 1) + X * (j + 1) + P * (k + 1)]; });
-      });
+      tail_quads(Cc, [&](int ci, int cj, int ck, int slot) {
+        return restrict_partial(L, Cc, ci, cj, ck, slot,
+                                [&](int i, int j, int k) { return u[(i + 1) + X * (j + 1) + P * (k + 1)]; });
+      }, [&](int ci, int cj, int ck, T sum) { rc[(ci + 1) + CX * (cj + 1) + CP * (ck + 1)] = sum; });
       __syncthreads();
       continue;
     }

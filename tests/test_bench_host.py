@@ -18,6 +18,17 @@ def test_step_traffic_sums_bytes_times_launches():
     assert r["achieved"] == (fixed + 2.5 * per_iter) / 1e-6 / 1e9
 
 
+def test_dominant_kernel_weights_cg_kernels_by_the_mean_iterations():
+    # profiled step with 4 CG iterations; the timed steps averaged 2.5: "cg"
+    # (0.3 ms per launch, once per iteration) takes 0.75 ms per average step,
+    # "fix" (one 1.0 ms launch) 1.0 ms -- although "cg" led the profiled step
+    kernels = {"cg": {"total_ms": 1.2, "launches": 4}, "fix": {"total_ms": 1.0, "launches": 1}}
+    name, _, ms, share = bench.dominant_kernel(kernels, prof_iters=4, mean_iters=2.5)
+    assert name == "fix" and ms == 1.0 and abs(share - 1.0 / 1.75) < 1e-12
+    name, _, ms, _ = bench.dominant_kernel(kernels, prof_iters=4, mean_iters=4.0)
+    assert name == "cg" and abs(ms - 1.2) < 1e-12
+
+
 def test_step_traffic_never_raises():
     assert "error" in bench.step_traffic({"a": {}}, 1, 1.0, 1.0, 1.0, 1)
     assert "error" in bench.step_traffic({"a": {"bytes_per_launch": 1.0, "launches": 1}}, 1, 1.0, 0.0, 1.0, 1)
