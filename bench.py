@@ -568,23 +568,25 @@ def run_large(args):
     del x0
     warm = 3
     first = g32.step()
-    g32.run(warm - 1, stats=False)
-    g64.run(warm, stats=False)
+    its0 = {id(g32): g32.run(warm - 1).cg_iters_total, id(g64): g64.run(warm).cg_iters_total}
     snap_at = steps - adj_steps
+
+    mean_its = {}
 
     def timed(g, n, snapshot=None):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ms, done, snap = 0.0, 0, None
+        ms, done, snap, last = 0.0, 0, None, None
         for chunk in ([snapshot - warm, n - snapshot] if snapshot else [n - warm]):
             torch.cuda.synchronize()
             e0.record(g.stream)
-            g.run(chunk, stats=False)
+            last = g.run(chunk)
             e1.record(g.stream)
             torch.cuda.synchronize()
             ms += e0.elapsed_time(e1)
             done += chunk
             if snapshot and snap is None:
                 snap = g.state()
+        mean_its[id(g)] = (last.cg_iters_total - its0[id(g)]) / done
         return ms, done, snap
 
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
@@ -602,13 +604,13 @@ def run_large(args):
     fp64_peak = 152 * 2 * 2 * 2070e6          # SMs x FP64 FMA/clk/SM x 2 flops x max SM clock
 
     def roofline(g, fp64=False):
-        _, kernels = g.profile_step()
-        name, k = max(kernels.items(), key=lambda kv: kv[1]["total_ms"])
+        pst, kernels = g.profile_step()
+        name, k, _, share = dominant_kernel(kernels, pst.cg_iters, mean_its[id(g)])
         avg_s = k["total_ms"] / k["launches"] * 1e-3
         out = {"bound": "hbm", "kernel": name, "achieved": k["bytes_per_launch"] / avg_s / 1e9, "peak": peak,
                "unit": "GB/s", "peak_source": f"hbm_gbs of {peak_kind}",
-               "kernel_share_of_step": k["total_ms"] / sum(x["total_ms"] for x in kernels.values()),
-               "avg_launch_us": avg_s * 1e6}
+               "kernel_share_of_step": share, "avg_launch_us": avg_s * 1e6,
+               "cg_iters_mean": mean_its[id(g)]}
         out["frac"] = out["achieved"] / peak
         if fp64:
             fpc = fp64_flops_per_cell(name)
