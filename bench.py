@@ -473,7 +473,9 @@ def preconditioner_table(steps: int = 10):
     import torch
     from paper_2204_01117_gb300 import layouts, uf
     sc = layouts.urban_block(NX, NY, NZ, seed=0)
-    cases = [("mg", dict(precond="mg", mg_smoother="cheby")), ("mg-jacobi", dict(precond="mg", mg_smoother="jacobi")),
+    cases = [("mg", dict(precond="mg", mg_smoother="cheby")),
+             ("mg-constant-transfers", dict(precond="mg", mg_smoother="cheby", mg_transfer="constant")),
+             ("mg-jacobi", dict(precond="mg", mg_smoother="jacobi")),
              ("mg-rbgs", dict(precond="mg", mg_smoother="rbgs")), ("ai2", dict(precond="ai2")),
              ("ai1", dict(precond="ai1")), ("jacobi", dict(precond="jacobi")), ("none", dict(precond="none")),
              ("ai2-paper-rule", dict(precond="ai2", cg_stop_rule="paper")),
