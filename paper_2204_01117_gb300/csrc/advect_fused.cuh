@@ -5,10 +5,10 @@
 // of lattice points (the same index range on the u, v and w lattices) and
 // marches along z.  It stages, in shared memory:
 //   * the time-level-n fields u, v, w on the column plus a halo of 2
-//     (36 x 12 per plane, a ring of 5 planes per component), copied one
+//     (36 x 12 per plane, a ring of 8 planes per component, 5 of them live), copied one
 //     plane ahead with cp.async;
 //   * the forward-step values phi^ = phi(x - dt u(x)) of each component on
-//     the column plus a halo of 1 (34 x 10 per plane, a ring of 3 planes).
+//     the column plus a halo of 1 (34 x 10 per plane, a ring of 4 planes, 3 live).
 // The backward step, the correction phi* = phi^ + (phi - phi^(x + dt u(x)))/2
 // and the clamp to the range of the forward sample's 8 values then read
 // both from shared memory.  Per plane: two barriers (see advect_fused_body).
@@ -34,7 +34,10 @@ namespace uf {
 constexpr int MX = 32, MY = 8, MT = MX * MY;                    // owned column, threads per block
 constexpr int MWX = MX + 4, MWY = MY + 4, MWP = MWX * MWY;      // window of the fields (halo 2)
 constexpr int MHX = MX + 2, MHY = MY + 2, MHP = MHX * MHY;      // window of phi^ (halo 1)
-constexpr int MFR = 5, MHR = 3;                                 // ring depths (planes)
+// ring depths (planes): 5 and 3 are live; powers of two make the slot of plane
+// kk (kk >= -2) a bit mask instead of a division
+constexpr int MFR = 8, MHR = 4;
+static_assert((MFR & (MFR - 1)) == 0 && (MHR & (MHR - 1)) == 0, "ring depths are powers of two");
 #ifndef UF_ADVECT_MINB
 #define UF_ADVECT_MINB 2   // resident blocks per SM the register budget is sized for
 #endif
@@ -45,12 +48,12 @@ constexpr size_t advect_fused_smem() {
 }
 
 // Staged planes [zlo, zhi] of a W x H window with lattice origin (ox, oy),
-// held in a ring of R planes (plane kk in slot (kk + 4R) mod R; kk >= -2).
+// held in a ring of R planes (R a power of two: plane kk in slot kk & (R - 1)).
 template <typename T, int W, int H, int R>
 struct Win {
   const T* ring;
   int ox, oy, zlo, zhi;
-  __device__ __forceinline__ const T* plane(int kk) const { return ring + ((kk + 4 * R) % R) * (W * H); }
+  __device__ __forceinline__ const T* plane(int kk) const { return ring + (kk & (R - 1)) * (W * H); }
   __device__ __forceinline__ bool holds(int i0, int i1, int j0, int j1, int k0, int k1) const {
     return i0 >= ox && i1 < ox + W && j0 >= oy && j1 < oy + H && k0 >= zlo && k1 <= zhi;
   }
@@ -121,7 +124,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <typename T>
 __device__ __forceinline__ void stage_plane(const AdvectArgs<T>& A, T* sF, int i0, int j0, int kk) {
   if (kk < 0) return;
-  const int slot = (kk + 4 * MFR) % MFR;
+  const int slot = kk & (MFR - 1);
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int t = threadIdx.x + h * MT;
@@ -207,7 +210,7 @@ __device__ __forceinline__ void fhat_point(const AdvectArgs<T>& A, const FWins<T
       if (ox && oy && oz) tape[(size_t)gi + (size_t)L.P * ((size_t)gj + (size_t)L.Ly * m)] = val;
     }
   }
-  sH[(Q * MHR + (m + 4 * MHR) % MHR) * MHP + t] = val;
+  sH[(Q * MHR + (m & (MHR - 1))) * MHP + t] = val;
 }
 
 // phi^ on plane m over the halo-1 window: 3 x MHP items (component,
@@ -256,7 +259,7 @@ __device__ __forceinline__ void maccormack_point(const AdvectArgs<T>& A, const T
     f[6] = fh_global(A, Q, L, F, a0, b1, c1, s); f[7] = fh_global(A, Q, L, F, a1, b1, c1, s);
   }
   const T bwd = trilerp<T, false>(f, ta, tb, tc, nullptr, nullptr);
-  const T own = sF[(Q * MFR + (k + 4 * MFR) % MFR) * MWP + (gi - i0 + 2) + MWX * (gj - j0 + 2)];
+  const T own = sF[(Q * MFR + (k & (MFR - 1))) * MWP + (gi - i0 + 2) + MWX * (gj - j0 + 2)];
   const T r = fwd + T(0.5) * (own - bwd);
   out_of<Q>(A)[(size_t)gi + (size_t)L.P * ((size_t)gj + (size_t)L.Ly * k)] = fmin(fmax(r, mn), mx);
 }
