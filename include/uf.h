@@ -52,7 +52,9 @@ typedef enum {
   UF_ERR_NOT_CONVERGED = 4,  /* pressure CG hit its iteration cap           */
   UF_ERR_NAN = 5,            /* non-finite residual in the pressure solve   */
   UF_ERR_TIMEOUT = 6,        /* a bounded device wait gave up               */
-  UF_ERR_STATE = 7           /* call out of order (e.g. step before init)   */
+  UF_ERR_STATE = 7,          /* call out of order (e.g. step before init)   */
+  UF_ERR_BOUNDS = 8          /* an index left its array (only in a library
+                                built with -DUF_BOUNDS_CHECK)              */
 } uf_status;
 
 enum { UF_F32 = 0,   /* FP32 fields, FP64 reductions and coarsest MG solve */
@@ -524,6 +526,11 @@ uf_status uf_poisson_solve_static(int nx, int ny, int nz, double wind_dir_deg, c
 
 /* Thread-local message of the last failure. */
 const char* uf_last_error(void);
+
+/* 1 if this library was built with -DUF_BOUNDS_CHECK (the debug build whose
+ * kernels check every global index they form against its array and whose
+ * calls then return UF_ERR_BOUNDS on a violation), else 0. */
+int uf_bounds_checked(void);
 
 #ifdef __cplusplus
 }

@@ -27,6 +27,8 @@ void uf_internal_set_last_error(const char* msg);
 
 struct uf_batch {
   virtual ~uf_batch() {}
+  // Status of a finished entry point (see uf_grid::after_call).
+  virtual uf_status after_call(uf_status s) { return s; }
   virtual uf_status grid(int, uf_grid**) = 0;
   virtual uf_status run(int, uf_step_stats*) = 0;
   virtual uf_status launch_counts(int*, int*) = 0;
@@ -483,6 +485,7 @@ class BatchImpl final : public uf_batch {
       launch();
       return;
     }
+    NvtxRange range(name.c_str());   // eager profiled step: one range per launch
     if (pool_used + 2 > pool.size())
       for (int k = 0; k < 2; ++k) {
         cudaEvent_t e;
@@ -902,6 +905,14 @@ class BatchImpl final : public uf_batch {
     return UF_OK;
   }
 
+  uf_status after_call(uf_status s) override {
+#ifdef UF_BOUNDS_CHECK
+    uf::BoundsHit h;
+    if (uf::bounds_hit_take(stream, &h)) return bfail(UF_ERR_BOUNDS, bounds_text(h));
+#endif
+    return s;
+  }
+
   uf_status run(int nsteps, uf_step_stats* stats) override {
     if (nsteps < 0) return bfail(UF_ERR_ARG, "nsteps < 0");
     for (int i = 0; i < n; ++i)
@@ -1033,7 +1044,8 @@ uf_status uf_batch_grid(uf_batch* b, int i, uf_grid** out) {
 
 uf_status uf_batch_run(uf_batch* b, int nsteps, uf_step_stats* stats) {
   if (!b) return bfail(UF_ERR_ARG, "NULL batch");
-  return b->run(nsteps, stats);
+  NvtxRange range("uf_batch_run");
+  return b->after_call(b->run(nsteps, stats));
 }
 
 uf_status uf_batch_launch_counts(uf_batch* b, int* fixed, int* per_iter) {
@@ -1044,13 +1056,15 @@ uf_status uf_batch_launch_counts(uf_batch* b, int* fixed, int* per_iter) {
 uf_status uf_batch_autotune(uf_batch* b, int reps, int* classes) {
   if (!b) return bfail(UF_ERR_ARG, "NULL batch");
   if (reps < 1) return bfail(UF_ERR_ARG, "reps >= 1 required");
-  return b->autotune(reps, classes);
+  NvtxRange range("uf_batch_autotune");
+  return b->after_call(b->autotune(reps, classes));
 }
 
 uf_status uf_batch_profile_step(uf_batch* b, uf_kernel_time* out, int capacity, int* count) {
   if (!b) return bfail(UF_ERR_ARG, "NULL batch");
   if (capacity < 0) return bfail(UF_ERR_ARG, "negative capacity");
-  return b->profile_step(out, capacity, count);
+  NvtxRange range("uf_batch_profile_step");
+  return b->after_call(b->profile_step(out, capacity, count));
 }
 
 uf_status uf_batch_destroy(uf_batch* b) {

@@ -509,6 +509,14 @@ class GridImpl final : public uf_grid {
     }
     return pool[pool_used++];
   }
+  uf_status after_call(uf_status s) override {
+#ifdef UF_BOUNDS_CHECK
+    uf::BoundsHit h;
+    if (uf::bounds_hit_take(stream, &h)) return fail(UF_ERR_BOUNDS, bounds_text(h));
+#endif
+    return s;
+  }
+
   template <typename F>
   void L(cudaStream_t s, const std::string& name, double bytes, F launch) {
     rec_count++;
@@ -516,6 +524,7 @@ class GridImpl final : public uf_grid {
       launch();
       return;
     }
+    NvtxRange range(name.c_str());   // eager profiled step: one range per launch
     Rec r{name, bytes, next_event(), next_event()};
     cudaEventRecord(r.a, s);
     launch();
@@ -2348,93 +2357,95 @@ uf_status uf_destroy(uf_grid* g) {
 
 #define UF_NEED(g) if (!(g)) return fail(UF_ERR_ARG, "NULL grid")
 
-uf_status uf_set_porosity(uf_grid* g, const void* phi) { UF_NEED(g); return g->set_porosity(phi); }
-uf_status uf_set_state(uf_grid* g, int f, const void* b) { UF_NEED(g); return g->set_state(f, b); }
-uf_status uf_get_state(uf_grid* g, int f, void* b) { UF_NEED(g); return g->get_state(f, b); }
-uf_status uf_init_state(uf_grid* g) { UF_NEED(g); return g->init_state(); }
-uf_status uf_step(uf_grid* g, uf_step_stats* s) { UF_NEED(g); return g->step(s); }
-uf_status uf_run(uf_grid* g, int n, uf_step_stats* s) { UF_NEED(g); return g->run(n, s); }
+// Every entry point that works on a grid runs inside an NVTX range named
+// after it (seen by Nsight Systems and other NVTX tools; next to free
+// without one), and hands its status to after_call, which in a library built
+// with -DUF_BOUNDS_CHECK reports an out-of-bounds index (UF_ERR_BOUNDS).
+#define UF_CALL(g, name, expr)         \
+  do {                                 \
+    UF_NEED(g);                        \
+    NvtxRange nvtx_range_(name);       \
+    return (g)->after_call(expr);      \
+  } while (0)
+
+uf_status uf_set_porosity(uf_grid* g, const void* phi) { UF_CALL(g, "uf_set_porosity", g->set_porosity(phi)); }
+uf_status uf_set_state(uf_grid* g, int f, const void* b) { UF_CALL(g, "uf_set_state", g->set_state(f, b)); }
+uf_status uf_get_state(uf_grid* g, int f, void* b) { UF_CALL(g, "uf_get_state", g->get_state(f, b)); }
+uf_status uf_init_state(uf_grid* g) { UF_CALL(g, "uf_init_state", g->init_state()); }
+uf_status uf_step(uf_grid* g, uf_step_stats* s) { UF_CALL(g, "uf_step", g->step(s)); }
+uf_status uf_run(uf_grid* g, int n, uf_step_stats* s) { UF_CALL(g, "uf_run", g->run(n, s)); }
 uf_status uf_objective(uf_grid* g, double z_lo, double z_hi, double u_hi, double u_lo, double* J) {
-  UF_NEED(g);
-  return g->objective(z_lo, z_hi, u_hi, u_lo, J);
+  UF_CALL(g, "uf_objective", g->objective(z_lo, z_hi, u_hi, u_lo, J));
 }
-uf_status uf_divergence(uf_grid* g, double* out) { UF_NEED(g); return g->divergence(out); }
-uf_status uf_apply_poisson(uf_grid* g, const void* x, void* y) { UF_NEED(g); return g->apply_poisson(x, y); }
+uf_status uf_divergence(uf_grid* g, double* out) { UF_CALL(g, "uf_divergence", g->divergence(out)); }
+uf_status uf_apply_poisson(uf_grid* g, const void* x, void* y) { UF_CALL(g, "uf_apply_poisson", g->apply_poisson(x, y)); }
 uf_status uf_poisson_solve(uf_grid* g, const void* b, int* iters, double* rel) {
-  UF_NEED(g);
-  return g->poisson_solve(b, iters, rel);
+  UF_CALL(g, "uf_poisson_solve", g->poisson_solve(b, iters, rel));
 }
 int uf_last_step_launches(uf_grid* g) { return g ? g->last_launches() : 0; }
-uf_status uf_launch_counts(uf_grid* g, int* fixed, int* per_iter) { UF_NEED(g); return g->launch_counts(fixed, per_iter); }
+uf_status uf_launch_counts(uf_grid* g, int* fixed, int* per_iter) { UF_CALL(g, "uf_launch_counts", g->launch_counts(fixed, per_iter)); }
 uf_status uf_profile_step(uf_grid* g, uf_kernel_time* out, int capacity, int* count, uf_step_stats* stats) {
-  UF_NEED(g);
   if (capacity < 0) return fail(UF_ERR_ARG, "negative capacity");
-  return g->profile_step(out, capacity, count, stats);
+  UF_CALL(g, "uf_profile_step", g->profile_step(out, capacity, count, stats));
 }
 size_t uf_adjoint_workspace_bytes(uf_grid* g, int nsteps, int ckpt_every) {
   return g ? g->adjoint_bytes(nsteps, ckpt_every) : 0;
 }
 uf_status uf_adjoint_run(uf_grid* g, void* ws, size_t bytes, int nsteps, int ckpt_every, double z_lo, double z_hi,
                          double u_hi, double u_lo, void* dJ_dphi, double* J_out) {
-  UF_NEED(g);
-  return g->adjoint_run(ws, bytes, nsteps, ckpt_every, z_lo, z_hi, u_hi, u_lo, dJ_dphi, J_out);
+  UF_CALL(g, "uf_adjoint_run", g->adjoint_run(ws, bytes, nsteps, ckpt_every, z_lo, z_hi, u_hi, u_lo, dJ_dphi, J_out));
 }
 uf_status uf_set_fields(uf_grid* g, int n, const int* fields, const void* const* bufs) {
-  UF_NEED(g);
-  return g->set_fields(n, fields, bufs);
+  UF_CALL(g, "uf_set_fields", g->set_fields(n, fields, bufs));
 }
 size_t uf_state_bytes(uf_grid* g) { return g ? g->state_bytes() : 0; }
-uf_status uf_save_state(uf_grid* g, void* buf, size_t bytes) { UF_NEED(g); return g->save_snapshot(buf, bytes); }
-uf_status uf_load_state(uf_grid* g, const void* buf, size_t bytes) { UF_NEED(g); return g->load_snapshot(buf, bytes); }
+uf_status uf_save_state(uf_grid* g, void* buf, size_t bytes) { UF_CALL(g, "uf_save_state", g->save_snapshot(buf, bytes)); }
+uf_status uf_load_state(uf_grid* g, const void* buf, size_t bytes) { UF_CALL(g, "uf_load_state", g->load_snapshot(buf, bytes)); }
 uf_status uf_get_fields(uf_grid* g, int n, const int* fields, void* const* bufs) {
-  UF_NEED(g);
-  return g->get_fields(n, fields, bufs);
+  UF_CALL(g, "uf_get_fields", g->get_fields(n, fields, bufs));
 }
 uf_status uf_objective_ex(uf_grid* g, const uf_objective_desc* obj, double* J_out) {
-  UF_NEED(g);
-  return g->objective_ex(obj, J_out);
+  UF_CALL(g, "uf_objective_ex", g->objective_ex(obj, J_out));
 }
 uf_status uf_adjoint_run_ex(uf_grid* g, void* d_ws, size_t bytes, int nsteps, int ckpt_every,
                             const uf_objective_desc* obj, void* dJ_dphi, double* J_out) {
-  UF_NEED(g);
-  return g->adjoint_run_ex(d_ws, bytes, nsteps, ckpt_every, obj, dJ_dphi, J_out);
+  UF_CALL(g, "uf_adjoint_run_ex", g->adjoint_run_ex(d_ws, bytes, nsteps, ckpt_every, obj, dJ_dphi, J_out));
 }
 uf_status uf_mesh_to_phi(uf_grid* g, int ntri, const double* tris, int nobj, const int* obj_first,
                          const int* obj_count, const double* obj_phi, int sub, void* phi_out) {
-  UF_NEED(g);
-  return g->mesh_to_phi(ntri, tris, nobj, obj_first, obj_count, obj_phi, sub, phi_out);
+  UF_CALL(g, "uf_mesh_to_phi", g->mesh_to_phi(ntri, tris, nobj, obj_first, obj_count, obj_phi, sub, phi_out));
 }
 uf_status uf_substep(uf_grid* g, int which, int transpose, const void* const* in, const void* const* cot,
                      void* const* out) {
-  UF_NEED(g);
-  return g->substep(which, transpose, in, cot, out);
+  UF_CALL(g, "uf_substep", g->substep(which, transpose, in, cot, out));
 }
 uf_status uf_step_vjp(uf_grid* g, void* d_ws, size_t bytes, const void* const* lam_out, void* const* lam_in,
                       void* lam_phi) {
-  UF_NEED(g);
-  return g->step_vjp(d_ws, bytes, lam_out, lam_in, lam_phi);
+  UF_CALL(g, "uf_step_vjp", g->step_vjp(d_ws, bytes, lam_out, lam_in, lam_phi));
 }
 uf_status uf_get_tuning(uf_grid* g, uf_tuning* out, int* levels) {
-  UF_NEED(g);
-  return g->get_tuning(out, levels);
+  UF_CALL(g, "uf_get_tuning", g->get_tuning(out, levels));
 }
 uf_status uf_set_tuning(uf_grid* g, const uf_tuning* t) {
-  UF_NEED(g);
-  return g->set_tuning(t);
+  UF_CALL(g, "uf_set_tuning", g->set_tuning(t));
 }
 uf_status uf_autotune(uf_grid* g, int reps, uf_tuning* chosen, double* best_ms) {
-  UF_NEED(g);
-  return g->autotune(reps, chosen, best_ms);
+  UF_CALL(g, "uf_autotune", g->autotune(reps, chosen, best_ms));
 }
 uf_status uf_design_to_phi(uf_grid* g, int nbox, const double* boxes, const double* theta, double width, void* phi_out) {
-  UF_NEED(g);
-  return g->design_phi(nbox, boxes, theta, width, phi_out);
+  UF_CALL(g, "uf_design_to_phi", g->design_phi(nbox, boxes, theta, width, phi_out));
 }
 uf_status uf_design_vjp(uf_grid* g, int nbox, const double* boxes, const double* theta, double width,
                         const void* dJ_dphi, double* dJ_dtheta) {
-  UF_NEED(g);
-  return g->design_vjp(nbox, boxes, theta, width, dJ_dphi, dJ_dtheta);
+  UF_CALL(g, "uf_design_vjp", g->design_vjp(nbox, boxes, theta, width, dJ_dphi, dJ_dtheta));
 }
 const char* uf_last_error(void) { return g_err.c_str(); }
+int uf_bounds_checked(void) {
+#ifdef UF_BOUNDS_CHECK
+  return 1;
+#else
+  return 0;
+#endif
+}
 
 }  // extern "C"

@@ -3,6 +3,9 @@
 // view of one grid's device state that the batched kernels read.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
+
+#include <string>
 
 #include "../../include/uf.h"
 #include "mg_fused.cuh"
@@ -39,8 +42,26 @@ struct GridView {
   uf::SmoothW<T> sw;               // smoother weights
 };
 
+// An NVTX range (host side) for the lifetime of a scope.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// The message of a bounds-check record (UF_BOUNDS_CHECK builds).
+inline std::string bounds_text(const uf::BoundsHit& h) {
+  static const char* arrays[] = {"u lattice", "v lattice", "cell / w lattice", "multigrid level"};
+  return std::string("index out of its array: ") + (h.array >= 0 && h.array < 4 ? arrays[h.array] : "?") + " at (" +
+         std::to_string(h.i) + ", " + std::to_string(h.j) + ", " + std::to_string(h.k) + ")";
+}
+
 struct uf_grid {
   virtual ~uf_grid() {}
+  // Status of a finished entry point: s, or UF_ERR_BOUNDS where a library
+  // built with -DUF_BOUNDS_CHECK recorded an index outside its array.
+  virtual uf_status after_call(uf_status s) { return s; }
   virtual uf_status set_porosity(const void*) = 0;
   virtual uf_status set_state(int, const void*) = 0;
   virtual uf_status get_state(int, void*) = 0;

@@ -160,6 +160,15 @@ extern "C" uf_status uf_poisson_solve_static(int nx, int ny, int nz, double wind
   e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return static_fail(UF_ERR_CUDA, std::string("state read: ") + cudaGetErrorString(e));
+#ifdef UF_BOUNDS_CHECK
+  {
+    uf::BoundsHit bh;
+    if (uf::bounds_hit_take(s, &bh))
+      return static_fail(UF_ERR_BOUNDS, "index out of its array (" + std::to_string(bh.array) + ": " +
+                                            std::to_string(bh.i) + ", " + std::to_string(bh.j) + ", " +
+                                            std::to_string(bh.k) + ")");
+  }
+#endif
   if (iters) *iters = h.iter;
   if (rel_residual) *rel_residual = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
   if (h.status == uf::DEV_NOT_CONVERGED) return static_fail(UF_ERR_NOT_CONVERGED, "CG reached its iteration cap");

@@ -52,6 +52,7 @@ __device__ __forceinline__ T* level_r(const Level<T>& L, int iter) {
 
 template <typename T>
 __device__ __forceinline__ size_t lidx(const Level<T>& L, int i, int j, int k) {
+  UF_BOUNDS(i >= 0 && i < L.P && j >= 0 && j < L.ny && k >= 0 && k < L.nz, BA_LEVEL, i, j, k);
   return (size_t)i + (size_t)L.P * ((size_t)j + (size_t)L.ny * k);
 }
 

@@ -43,17 +43,64 @@ struct StepParams {
   const T* dtT;            // the same time step in the field type (read per cell)
 };
 
+// ------------------------------------------------------- bounds checks --
+// Debug build (compiled with -DUF_BOUNDS_CHECK): every global index the
+// index helpers form (idx_u, idx_v, idx_c here, lidx for the multigrid
+// levels) is checked against its array: x within the row pitch, y and z
+// within the stored rows and planes.  The first violation is recorded in
+// uf_bounds_hit (array, i, j, k) and the access is redirected to element 0,
+// so the kernel completes; the host reads the record after the call and
+// returns UF_ERR_BOUNDS.  Each translation unit has its own record, read by
+// its own host code.  The ordinary build compiles none of this.
+enum BoundsArray { BA_U = 0, BA_V = 1, BA_CW = 2, BA_LEVEL = 3 };
+struct BoundsHit {
+  int hit, array, i, j, k;
+};
+#ifdef UF_BOUNDS_CHECK
+static __device__ BoundsHit uf_bounds_hit;
+__device__ __forceinline__ void bounds_check(bool ok, int array, int& i, int& j, int& k) {
+  if (ok) return;
+  if (atomicExch(&uf_bounds_hit.hit, 1) == 0) {
+    uf_bounds_hit.array = array;
+    uf_bounds_hit.i = i;
+    uf_bounds_hit.j = j;
+    uf_bounds_hit.k = k;
+  }
+  i = j = k = 0;
+}
+// Reads (and clears) this translation unit's record after the work queued
+// on stream s; true if an index was out of bounds.
+static inline bool bounds_hit_take(cudaStream_t s, BoundsHit* out) {
+  const BoundsHit clear = {0, 0, 0, 0, 0};
+  if (cudaMemcpyFromSymbolAsync(out, uf_bounds_hit, sizeof(*out), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return false;   // (the CUDA error surfaces in the caller's next check)
+  if (!out->hit) return false;
+  cudaMemcpyToSymbolAsync(uf_bounds_hit, &clear, sizeof(clear), 0, cudaMemcpyHostToDevice, s);
+  cudaStreamSynchronize(s);
+  return true;
+}
+#define UF_BOUNDS(ok, array, i, j, k) ::uf::bounds_check((ok), (array), i, j, k)
+#else
+#define UF_BOUNDS(ok, array, i, j, k) ((void)0)
+#endif
+
 // ------------------------------------------------------------- indexing --
 template <typename T>
 __device__ __forceinline__ size_t idx_u(const StepParams<T>& p, int i, int j, int k) {
+  UF_BOUNDS(i >= 0 && i < p.Pu && j >= 0 && j < p.ny && k >= 0 && k < p.nz, BA_U, i, j, k);
   return (size_t)i + (size_t)p.Pu * ((size_t)j + (size_t)p.ny * k);
 }
 template <typename T>
 __device__ __forceinline__ size_t idx_v(const StepParams<T>& p, int i, int j, int k) {
+  UF_BOUNDS(i >= 0 && i < p.Pc && j >= 0 && j <= p.ny && k >= 0 && k < p.nz, BA_V, i, j, k);
   return (size_t)i + (size_t)p.Pc * ((size_t)j + (size_t)(p.ny + 1) * k);
 }
 template <typename T>   // w lattice and cell lattice share the x-y layout
 __device__ __forceinline__ size_t idx_c(const StepParams<T>& p, int i, int j, int k) {
+  // (z up to nz: the w lattice's top face; a cell array has nz planes, which
+  // this shared helper cannot tell apart)
+  UF_BOUNDS(i >= 0 && i < p.Pc && j >= 0 && j < p.ny && k >= 0 && k <= p.nz, BA_CW, i, j, k);
   return (size_t)i + (size_t)p.Pc * ((size_t)j + (size_t)p.ny * k);
 }
 

@@ -19,14 +19,16 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(_HERE)
 CSRC = os.path.join(_HERE, "csrc")
 LIB_PATH = os.path.join(_HERE, "_build", "libuf.so")
+# debug build with device-side bounds checks of every global index (-DUF_BOUNDS_CHECK)
+CHECKED_LIB_PATH = os.path.join(_HERE, "_build_checked", "libuf.so")
 HEADER = os.path.join(ROOT, "include", "uf.h")
 SOURCES = ["capi.cu", "noalloc.cu", "batch.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo",
               "--expt-extended-lambda", "-Xcompiler", "-fPIC", "-shared"]
 
-UF_OK, UF_ERR_ARG, UF_ERR_CUDA, UF_ERR_NOMEM, UF_ERR_NOT_CONVERGED, UF_ERR_NAN, UF_ERR_TIMEOUT, UF_ERR_STATE = range(8)
+UF_OK, UF_ERR_ARG, UF_ERR_CUDA, UF_ERR_NOMEM, UF_ERR_NOT_CONVERGED, UF_ERR_NAN, UF_ERR_TIMEOUT, UF_ERR_STATE, UF_ERR_BOUNDS = range(9)
 STATUS_NAMES = ["UF_OK", "UF_ERR_ARG", "UF_ERR_CUDA", "UF_ERR_NOMEM", "UF_ERR_NOT_CONVERGED", "UF_ERR_NAN",
-                "UF_ERR_TIMEOUT", "UF_ERR_STATE"]
+                "UF_ERR_TIMEOUT", "UF_ERR_STATE", "UF_ERR_BOUNDS"]
 F32, F64 = 0, 1
 PRECOND = {"mg": 0, "ai1": 1, "jacobi": 2, "none": 3, "ai2": 4}
 STOP_RULE = {"residual": 0, "paper": 1}
@@ -118,7 +120,7 @@ class KernelTime(ctypes.Structure):
 
 class UFError(RuntimeError):
     def __init__(self, status: int, msg: str):
-        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
         self.status = status
 
 
@@ -126,20 +128,25 @@ _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the CUDA sources into _build/libuf.so for sm_103a (nvcc)."""
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile the CUDA sources into _build/libuf.so for sm_103a (nvcc).
+    checked=True: the debug build with bounds checks of every global index
+    (-DUF_BOUNDS_CHECK; an index outside its array makes the call return
+    UF_ERR_BOUNDS) into _build_checked/libuf.so; load it by setting
+    UF_LIBRARY to that path before the first load()."""
+    lib_path = CHECKED_LIB_PATH if checked else LIB_PATH
     with _lock:
         srcs = [os.path.join(CSRC, s) for s in SOURCES]
         deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")] + [HEADER]
-        if (not force and os.path.exists(LIB_PATH)
-                and os.path.getmtime(LIB_PATH) >= max(os.path.getmtime(p) for p in deps)):
-            return LIB_PATH
-        os.makedirs(os.path.dirname(LIB_PATH), exist_ok=True)
+        if (not force and os.path.exists(lib_path)
+                and os.path.getmtime(lib_path) >= max(os.path.getmtime(p) for p in deps)):
+            return lib_path
+        os.makedirs(os.path.dirname(lib_path), exist_ok=True)
         tag = f".tmp{os.getpid()}"
         objs, procs = [], []
-        compile_flags = [f for f in NVCC_FLAGS if f != "-shared"]
+        compile_flags = [f for f in NVCC_FLAGS if f != "-shared"] + (["-DUF_BOUNDS_CHECK"] if checked else [])
         for src in srcs:   # translation units compile in parallel
-            obj = os.path.join(os.path.dirname(LIB_PATH), os.path.basename(src) + tag + ".o")
+            obj = os.path.join(os.path.dirname(lib_path), os.path.basename(src) + tag + ".o")
             cmd = ["nvcc", *compile_flags, "-c", src, "-o", obj]
             if verbose:
                 print(" ".join(cmd))
@@ -148,12 +155,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
         codes = [pr.wait() for pr in procs]
         if any(codes):
             raise subprocess.CalledProcessError(max(codes), "nvcc")
-        tmp = LIB_PATH + tag
+        tmp = lib_path + tag
         subprocess.check_call(["nvcc", "-shared", "-gencode", "arch=compute_103a,code=sm_103a", *objs, "-o", tmp])
         for obj in objs:
             os.remove(obj)
-        os.replace(tmp, LIB_PATH)
-        return LIB_PATH
+        os.replace(tmp, lib_path)
+        return lib_path
 
 
 def declared_functions() -> list[str]:
@@ -164,13 +171,16 @@ def declared_functions() -> list[str]:
 
 
 def load():
-    """Load _build/libuf.so; raises OSError when it has not been built."""
+    """Load _build/libuf.so (or the library the environment variable
+    UF_LIBRARY names, e.g. the bounds-checked build); raises OSError when it
+    has not been built."""
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise OSError(f"{LIB_PATH} is missing: run paper_2204_01117_gb300.uf.build() first")
-    lib = ctypes.CDLL(LIB_PATH)
+    path = os.environ.get("UF_LIBRARY") or LIB_PATH
+    if not os.path.exists(path):
+        raise OSError(f"{path} is missing: run paper_2204_01117_gb300.uf.build() first")
+    lib = ctypes.CDLL(path)
     vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     P = ctypes.POINTER
     lib.uf_default_desc.argtypes = [P(GridDesc)]
