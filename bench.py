@@ -161,12 +161,17 @@ DIGEST_HEADERS = ("mg_fused.cuh", "solver_kernels.cuh", "step_kernels.cuh", "uf_
 
 
 def source_digest():
-    """Digest of the device code of the profiled solver kernels."""
+    """Digest of the device code of the profiled solver kernels: the code
+    of the headers with comments and whitespace removed, so that an edit of
+    a comment does not retire a capture of unchanged kernels."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2204_01117_gb300", "csrc")
     for f in sorted(DIGEST_HEADERS):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)   # block comments
+        text = re.sub(r"//[^\n]*", " ", text)                  # line comments
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -174,11 +174,12 @@ __device__ __forceinline__ T resid(T D, T q, T x, T nbsum) {
 // restriction is the transpose: coarse cell p gathers its children 2p and
 // 2p + 1 (3/4, or the ghost-folded weight at the level's ends) and the
 // outer neighbours 2p - 1 and 2p + 2 (1/4).
-// Each transfer value is one FMA chain over the slots inside the level, z
-// outermost, then y, then x (slot s is cell base + s), with explicit
-// rounding; every weight and every product of three is exact in binary.  So
-// a value is the same bit for bit wherever it is formed (the pass kernels,
-// the tail, the cluster V-cycle).
+// A prolongation value is one FMA chain over the slots inside the level, z
+// outermost, then y, then x (slot s is cell base + s); a restriction value
+// is four such chains, one per z slot, added in slot order (restrict_lin).
+// The arithmetic is explicitly rounded, and every weight and every product
+// of three is exact in binary, so a value is the same bit for bit wherever
+// it is formed (the pass kernels, the tail, the batch, the cluster V-cycle).
 struct Taps {
   int base;    // cell index of slot 0
   int valid;   // bit s: slot s takes part

@@ -1,6 +1,8 @@
 """Host-side arithmetic of bench.py that the GPU run relies on (no GPU):
 the whole-step algorithmic traffic and the source digest of the profiled
 kernels."""
+import os
+
 import pytest
 
 import bench
@@ -32,6 +34,23 @@ def test_dominant_kernel_weights_cg_kernels_by_the_mean_iterations():
 def test_step_traffic_never_raises():
     assert "error" in bench.step_traffic({"a": {}}, 1, 1.0, 1.0, 1.0, 1)
     assert "error" in bench.step_traffic({"a": {"bytes_per_launch": 1.0, "launches": 1}}, 1, 1.0, 0.0, 1.0, 1)
+
+
+def test_digest_ignores_comments_but_not_code(tmp_path, monkeypatch):
+    import shutil
+    src = os.path.join(bench.ROOT, "paper_2204_01117_gb300", "csrc")
+    dst = tmp_path / "paper_2204_01117_gb300" / "csrc"
+    dst.mkdir(parents=True)
+    for f in bench.DIGEST_HEADERS:
+        shutil.copy(os.path.join(src, f), dst / f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    d0 = bench.source_digest()
+    with open(dst / "mg_fused.cuh", "a") as fh:
+        fh.write("\n// a note\n/* a block\n   comment */\n")
+    assert bench.source_digest() == d0
+    with open(dst / "mg_fused.cuh", "a") as fh:
+        fh.write("constexpr int an_extra_constant = 1;\n")
+    assert bench.source_digest() != d0
 
 
 def test_digest_covers_the_profiled_kernel_headers():
