@@ -26,6 +26,11 @@
 //
 // Tape (the adjoint's recompute sweep): when A.uh is not null, phi^ at every
 // lattice point the block owns is also written to A.uh, A.vh, A.wh.
+//
+// When A.nut is not null the kernel also forms the eddy viscosity (a1) of
+// the cells it owns from the staged time-level-n velocity, bit for bit what
+// k_eddy_viscosity gives (strain_sq_acc rounds explicitly), which the step
+// then does not launch.
 #pragma once
 #include "step_kernels.cuh"
 
@@ -264,6 +269,21 @@ __device__ __forceinline__ void maccormack_point(const AdvectArgs<T>& A, const T
   out_of<Q>(A)[(size_t)gi + (size_t)L.P * ((size_t)gj + (size_t)L.Ly * k)] = fmin(fmax(r, mn), mx);
 }
 
+// Eddy viscosity of cell (gi, gj, k) (the expressions of
+// eddy_viscosity_body) with the faces strain_sq reads taken from the staged
+// windows: planes k-1 .. k+2 of the fields are complete here.
+template <typename T>
+__device__ __forceinline__ void eddy_point(const AdvectArgs<T>& A, const T* sF, int gi, int gj, int k, int i0, int j0) {
+  auto at = [&](int q, int a, int b, int c) {
+    return sF[(q * MFR + (c & (MFR - 1))) * MWP + (a - i0 + 2) + MWX * (b - j0 + 2)];
+  };
+  const T S2 = strain_sq_acc<T>(
+      A.sp, gi, gj, k, [&](int a, int b, int c) { return at(0, a, b, c); },
+      [&](int a, int b, int c) { return at(1, a, b, c); }, [&](int a, int b, int c) { return at(2, a, b, c); });
+  const size_t c = idx_c(A.sp, gi, gj, k);
+  A.nut[c] = limited_nut(A.sp, A.kf[c], A.om[c], S2, *A.dtT);
+}
+
 template <typename T>
 constexpr size_t advect_fused_smem_total() {
   return advect_fused_smem<T>() + sizeof(T) * advect_keep_elems<T>();
@@ -299,6 +319,7 @@ __device__ __forceinline__ void advect_fused_body(const AdvectArgs<T>& A, int zc
     maccormack_point<0>(A, sF, sH, sK, gi, gj, k, s, i0, j0);
     maccormack_point<1>(A, sF, sH, sK, gi, gj, k, s, i0, j0);
     maccormack_point<2>(A, sF, sH, sK, gi, gj, k, s, i0, j0);
+    if (A.nut && gi < A.nx && gj < A.ny) eddy_point(A, sF, gi, gj, k, i0, j0);
   }
   cp_async_wait_all();
 }

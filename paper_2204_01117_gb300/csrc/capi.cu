@@ -852,6 +852,9 @@ class GridImpl final : public uf_grid {
     A.nx = d.nx; A.ny = d.ny; A.nz = d.nz;
     A.dtT = dtT;
     A.inv_h = (T)(1.0 / d.h);
+    A.nut = nullptr;   // the fused step sets these (eddy viscosity inside the advection)
+    A.kf = A.om = nullptr;
+    A.sp = sp;
     return A;
   }
 
@@ -869,19 +872,23 @@ class GridImpl final : public uf_grid {
       L(s, "cfl_dt", faces, [&] {
         uf::k_cfl_dt<T><<<kDtBlocks, 256, 0, s>>>(u, P.n_u, v, P.n_v, w, P.n_w, d.cfl * d.h, partials, &st->ticket[0], dt, dtT);
       });
-    L(s, "eddy_viscosity", faces + 3 * cells,
-      [&] { uf::k_eddy_viscosity<T><<<plane_grid(d.nx, d.ny, d.nz), blk, 0, s>>>(sp, u, v, w, kin, oin, nut); });
     const uf::AdvectArgs<T> A = advect_args();
     const dim3 ga = plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1);
     if (!(unfused & UF_UNFUSED_ADVECT)) {
+      // one pass: the eddy viscosity (k, omega -> nu_t) and both MacCormack passes
       uf::AdvectArgs<T> Af = A;
       if (!taping) Af.uh = Af.vh = Af.wh = nullptr;
+      Af.nut = nut;
+      Af.kf = kin;
+      Af.om = oin;
       int zc;
       const dim3 gf = advect_grid(&zc);
-      L(s, "advect_fused", 2 * faces, [&] {
+      L(s, "advect_fused", 2 * faces + 3 * cells, [&] {
         uf::k_advect_fused<T><<<gf, uf::MT, uf::advect_fused_smem_total<T>(), s>>>(Af, zc);
       });
     } else {
+      L(s, "eddy_viscosity", faces + 3 * cells,
+        [&] { uf::k_eddy_viscosity<T><<<plane_grid(d.nx, d.ny, d.nz), blk, 0, s>>>(sp, u, v, w, kin, oin, nut); });
       L(s, "advect_forward", 2 * faces, [&] { uf::k_advect_forward<T><<<ga, blk, 0, s>>>(A); });
       L(s, "advect_backward", 3 * faces, [&] { uf::k_advect_backward<T><<<ga, blk, 0, s>>>(A); });
     }

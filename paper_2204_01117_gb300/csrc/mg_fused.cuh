@@ -141,16 +141,9 @@ __device__ __forceinline__ float rdiag(float D) {
 }
 __device__ __forceinline__ double rdiag(double D) { return 1.0 / D; }
 
-// Arithmetic with every operation rounded as written (the compiler fuses no
-// multiply into an add on its own): the smoother and residual expressions
-// below are shared by the per-level kernels and the cluster V-cycle, and
-// this way both compute them alike, bit for bit.
-__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+// (add_rn, mul_rn, fma_rn: uf_device.cuh.)  The smoother and residual
+// expressions below are shared by the per-level kernels and the cluster
+// V-cycle and spelled with them, so both compute them alike, bit for bit.
 
 // w_x (a1 + a2) + w_y (b1 + b2) + w_z (c1 + c2): the weighted sum of the six
 // neighbours of a cell (x pair, y pair, z pair).

@@ -76,22 +76,25 @@ __global__ void __launch_bounds__(256) k_cfl_dt(const T* __restrict__ u, size_t 
 // stored: diagonal terms from the two faces of the cell, off-diagonal terms
 // from central differences of cell-averaged velocities (one-sided at the
 // domain edge, zero for an extent of 1).
-template <typename T>
-__device__ __forceinline__ T strain_sq(const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ w,
-                                       const StepParams<T>& p, int i, int j, int k) {
+// uf(a, b, c), vf, wf: the face velocities; from global memory (strain_sq)
+// or from staged windows (the fused advection), with the same result: the
+// sum of squares is spelled with explicitly rounded operations, the rest
+// has nothing the compiler could fuse.
+template <typename T, typename UF, typename VF, typename WF>
+__device__ __forceinline__ T strain_sq_acc(const StepParams<T>& p, int i, int j, int k, UF uf, VF vf, WF wf) {
   const T ih = p.inv_h;
-  auto uc = [&](int a, int b, int c) { return T(0.5) * (u[idx_u(p, a, b, c)] + u[idx_u(p, a + 1, b, c)]); };
-  auto vc = [&](int a, int b, int c) { return T(0.5) * (v[idx_v(p, a, b, c)] + v[idx_v(p, a, b + 1, c)]); };
-  auto wc = [&](int a, int b, int c) { return T(0.5) * (w[idx_c(p, a, b, c)] + w[idx_c(p, a, b, c + 1)]); };
+  auto uc = [&](int a, int b, int c) { return T(0.5) * (uf(a, b, c) + uf(a + 1, b, c)); };
+  auto vc = [&](int a, int b, int c) { return T(0.5) * (vf(a, b, c) + vf(a, b + 1, c)); };
+  auto wc = [&](int a, int b, int c) { return T(0.5) * (wf(a, b, c) + wf(a, b, c + 1)); };
   const int im = i > 0 ? i - 1 : i, ip = i < p.nx - 1 ? i + 1 : i;
   const int jm = j > 0 ? j - 1 : j, jp = j < p.ny - 1 ? j + 1 : j;
   const int km = k > 0 ? k - 1 : k, kp = k < p.nz - 1 ? k + 1 : k;
   const T sx = (ip > im) ? ih / T(ip - im) : T(0);
   const T sy = (jp > jm) ? ih / T(jp - jm) : T(0);
   const T sz = (kp > km) ? ih / T(kp - km) : T(0);
-  const T sxx = (u[idx_u(p, i + 1, j, k)] - u[idx_u(p, i, j, k)]) * ih;
-  const T syy = (v[idx_v(p, i, j + 1, k)] - v[idx_v(p, i, j, k)]) * ih;
-  const T szz = (w[idx_c(p, i, j, k + 1)] - w[idx_c(p, i, j, k)]) * ih;
+  const T sxx = (uf(i + 1, j, k) - uf(i, j, k)) * ih;
+  const T syy = (vf(i, j + 1, k) - vf(i, j, k)) * ih;
+  const T szz = (wf(i, j, k + 1) - wf(i, j, k)) * ih;
   const T du_dy = (uc(i, jp, k) - uc(i, jm, k)) * sy;
   const T du_dz = (uc(i, j, kp) - uc(i, j, km)) * sz;
   const T dv_dx = (vc(ip, j, k) - vc(im, j, k)) * sx;
@@ -99,7 +102,16 @@ __device__ __forceinline__ T strain_sq(const T* __restrict__ u, const T* __restr
   const T dw_dx = (wc(ip, j, k) - wc(im, j, k)) * sx;
   const T dw_dy = (wc(i, jp, k) - wc(i, jm, k)) * sy;
   const T sxy = T(0.5) * (du_dy + dv_dx), sxz = T(0.5) * (du_dz + dw_dx), syz = T(0.5) * (dv_dz + dw_dy);
-  return sxx * sxx + syy * syy + szz * szz + T(2) * (sxy * sxy + sxz * sxz + syz * syz);
+  const T diag = fma_rn(szz, szz, fma_rn(syy, syy, mul_rn(sxx, sxx)));
+  const T off = fma_rn(syz, syz, fma_rn(sxz, sxz, mul_rn(sxy, sxy)));
+  return fma_rn(T(2), off, diag);
+}
+template <typename T>
+__device__ __forceinline__ T strain_sq(const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ w,
+                                       const StepParams<T>& p, int i, int j, int k) {
+  return strain_sq_acc<T>(
+      p, i, j, k, [&](int a, int b, int c) { return u[idx_u(p, a, b, c)]; },
+      [&](int a, int b, int c) { return v[idx_v(p, a, b, c)]; }, [&](int a, int b, int c) { return w[idx_c(p, a, b, c)]; });
 }
 
 // k-omega eddy viscosity with the strain limiter on omega (Sec. 3) and the
@@ -228,6 +240,12 @@ struct AdvectArgs {
   int nx, ny, nz;
   const T* dtT;
   T inv_h;
+  // fused advection only: with nut set, it also forms the eddy viscosity of
+  // the cells (a1, from the time-level-n velocity it stages) from kf, om
+  T* nut;
+  const T* kf;
+  const T* om;
+  StepParams<T> sp;
 };
 
 // Displacement in lattice units (dt/h * velocity) at a lattice point of

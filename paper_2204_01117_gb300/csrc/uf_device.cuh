@@ -43,6 +43,16 @@ struct StepParams {
   const T* dtT;            // the same time step in the field type (read per cell)
 };
 
+// Arithmetic with every operation rounded as written (the compiler fuses no
+// multiply into an add on its own): expressions that two kernels must form
+// alike, bit for bit, are spelled with these.
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // ------------------------------------------------------- bounds checks --
 // Debug build (compiled with -DUF_BOUNDS_CHECK): every global index the
 // index helpers form (idx_u, idx_v, idx_c here, lidx for the multigrid
