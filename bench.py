@@ -155,9 +155,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# The headers the profiled solver kernels are compiled from (mg_fused.cuh and
-# what it includes); host-side launch code and other kernels are outside.
-DIGEST_HEADERS = ("mg_fused.cuh", "solver_kernels.cuh", "step_kernels.cuh", "uf_device.cuh")
+# The headers the profiled kernels are compiled from (the multigrid and CG
+# kernels, the fused advection and momentum pass, and what they include);
+# host-side launch code and other kernels are outside.
+DIGEST_HEADERS = ("mg_fused.cuh", "solver_kernels.cuh", "step_kernels.cuh", "uf_device.cuh", "advect_fused.cuh",
+                  "momentum_fused.cuh")
+# committed ncu summaries with a table of DRAM bytes per launch
+TRAFFIC_PROFILES = ("mg_pcg_urban256.md", "advect_momentum_urban256.md")
 
 
 def source_digest():
@@ -176,22 +180,24 @@ def source_digest():
 
 
 def ncu_traffic(kernel_label: str):
-    """DRAM bytes per launch of a kernel from the committed ncu summary, or
-    None when the summary is missing or the kernel sources changed since."""
-    p = os.path.join(ROOT, "profiles", "mg_pcg_urban256.md")
-    if not os.path.exists(p):
-        return None
-    text = open(p).read()
-    m = re.search(r"source digest:\s*`([0-9a-f]+)`", text)
-    if not m or m.group(1) != source_digest():
-        return None
-    for line in text.splitlines():
-        cells = [c.strip() for c in line.strip().strip("|").split("|")]
-        if len(cells) >= 3 and cells[0] == kernel_label:
-            try:
-                return float(cells[2])
-            except ValueError:
-                return None
+    """DRAM bytes per launch of a kernel from a committed ncu summary (a
+    table row: label | ncu kernel | DRAM bytes | ...), or None when no
+    summary has it or the kernel sources changed since its capture."""
+    for name in TRAFFIC_PROFILES:
+        p = os.path.join(ROOT, "profiles", name)
+        if not os.path.exists(p):
+            continue
+        text = open(p).read()
+        m = re.search(r"source digest:\s*`([0-9a-f]+)`", text)
+        if not m or m.group(1) != source_digest():
+            continue
+        for line in text.splitlines():
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) >= 3 and cells[0] == kernel_label:
+                try:
+                    return float(cells[2])
+                except ValueError:
+                    return None
     return None
 
 
@@ -990,6 +996,16 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+    # the finest-level CG kernel, the bandwidth-bound one, when another kernel
+    # (the issue-bound fused advection) leads the step
+    cg = kernels.get("mg_down_cg_L0")
+    if cg and dom_name != "mg_down_cg_L0":
+        cg_ms = cg["total_ms"] / cg["launches"]
+        cg_gbs = cg["bytes_per_launch"] / (cg_ms * 1e-3) / 1e9
+        line["roofline_solver"] = {"bound": "hbm", "kernel": "mg_down_cg_L0", "achieved": cg_gbs, "peak": peak,
+                                   "unit": "GB/s", "frac": cg_gbs / peak, "traffic": ncu_traffic("mg_down_cg_L0"),
+                                   "peak_source": f"hbm_gbs of {peak_kind}",
+                                   "bytes_per_launch": cg["bytes_per_launch"], "avg_launch_us": cg_ms * 1e3}
     if not args.no_adjoint:
         line["adjoint"] = adjoint_leg()
     if not args.no_batched:

@@ -55,8 +55,10 @@ def test_digest_ignores_comments_but_not_code(tmp_path, monkeypatch):
 
 def test_digest_covers_the_profiled_kernel_headers():
     assert len(bench.source_digest()) == 16
-    assert set(bench.DIGEST_HEADERS) == {"mg_fused.cuh", "solver_kernels.cuh", "step_kernels.cuh", "uf_device.cuh"}
+    assert set(bench.DIGEST_HEADERS) == {"mg_fused.cuh", "solver_kernels.cuh", "step_kernels.cuh", "uf_device.cuh",
+                                         "advect_fused.cuh", "momentum_fused.cuh"}
     # the committed ncu summaries are read (None once the device code has
     # changed since the capture, by design)
-    for v in (bench.ncu_traffic("mg_down_cg_L0"), bench.fp64_flops_per_cell("mg_down_cg_L0")):
+    for v in (bench.ncu_traffic("mg_down_cg_L0"), bench.ncu_traffic("advect_fused"),
+              bench.fp64_flops_per_cell("mg_down_cg_L0")):
         assert v is None or v > 0
