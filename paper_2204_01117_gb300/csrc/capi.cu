@@ -918,7 +918,7 @@ class GridImpl final : public uf_grid {
     L(s, "pressure_commit", N() * 10 * tb(),
       [&] { uf::k_pressure_commit<T><<<plane_grid(d.nx, d.ny, d.nz), blk, 0, s>>>(sp, p, pd, gd, st); });
     L(s, "project", 2 * faces + 2 * cells,
-      [&] { uf::k_project<T><<<plane_grid(d.nx + 1, d.ny + 1, 3 * d.nz + 1), blk, 0, s>>>(sp, pd, u, v, w); });
+      [&] { uf::k_project_cells<T><<<plane_grid(d.nx + 1, d.ny + 1, d.nz), blk, 0, s>>>(sp, pd, u, v, w); });
     L(s, "turbulence", faces + 4 * cells,
       [&] { uf::k_turbulence<T><<<plane_grid(d.nx, d.ny, d.nz), blk, 0, s>>>(sp, u, v, w, kin, oin, kout, oout); });
   }

@@ -617,6 +617,38 @@ __global__ void __launch_bounds__(NT) k_project(StepParams<T> p, const PStore<T>
   project_body<T>(p, pr, u, v, w, vblock());
 }
 
+// The same projection with one thread per lattice column (i, j) of plane k
+// for the faces i, j and k of cell (i, j, k): the x, y and z faces that the
+// per-face form (project_body, blockIdx.z over the three components) gives
+// to three threads, with the same expression per face.  Grid (nx + 1, ny + 1)
+// columns by nz planes.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_project_cells(StepParams<T> p, const PStore<T>* __restrict__ pr,
+                                                      T* __restrict__ u, T* __restrict__ v, T* __restrict__ w) {
+  const VBlock vb = vblock();
+  const int i = vb.x * BX + threadIdx.x, j = vb.y * BY + threadIdx.y, k = vb.z;
+  const T g = *p.dtT / (p.rho * p.h);
+  const int nx = p.nx, ny = p.ny, nz = p.nz;
+  if (i <= nx && j < ny) {   // x face (i, j, k)
+    bool on = true;
+    T dp = 0;
+    if (i == 0) { on = p.side[0] == OUTFLOW; if (on) dp = (T)ps_value(pr[idx_c(p, 0, j, k)]); }
+    else if (i == nx) { on = p.side[1] == OUTFLOW; if (on) dp = -(T)ps_value(pr[idx_c(p, nx - 1, j, k)]); }
+    else dp = (T)ps_diff(pr[idx_c(p, i, j, k)], pr[idx_c(p, i - 1, j, k)]);
+    if (on) u[idx_u(p, i, j, k)] -= g * dp;
+  }
+  if (i < nx && j <= ny) {   // y face (i, j, k)
+    bool on = true;
+    T dp = 0;
+    if (j == 0) { on = p.side[2] == OUTFLOW; if (on) dp = (T)ps_value(pr[idx_c(p, i, 0, k)]); }
+    else if (j == ny) { on = p.side[3] == OUTFLOW; if (on) dp = -(T)ps_value(pr[idx_c(p, i, ny - 1, k)]); }
+    else dp = (T)ps_diff(pr[idx_c(p, i, j, k)], pr[idx_c(p, i, j - 1, k)]);
+    if (on) v[idx_v(p, i, j, k)] -= g * dp;
+  }
+  if (i < nx && j < ny && k >= 1)   // z face (i, j, k); k < nz here
+    w[idx_c(p, i, j, k)] -= g * (T)ps_diff(pr[idx_c(p, i, j, k)], pr[idx_c(p, i, j, k - 1)]);
+}
+
 
 // ------------------------------------------------------- a9: k-omega -----
 // Forward Euler for k and omega after the projection (Sec. 3): first-order
